@@ -1,0 +1,161 @@
+"""CPU oracle for the depth stage of arxiv 2201.11924 (Sec. VI-D).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The product package
+never imports this module, and this module never imports the product.
+
+The arithmetic lives in ``oracle.c`` (plain single-threaded C, int32 for the
+integer steps, fp64 for sub-pixel and depth); this file only compiles it with
+gcc and marshals numpy arrays through ctypes.
+
+Parity pins: every function here is pinned by ``tests/test_oracle_*.py``
+against facts that do not come from the oracle itself (hand-computed codes,
+invariants, brute-force minimum-energy label sequences, closed forms, exact
+disparity recovery on fronto-parallel planes).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Path index -> direction (rx, ry); the value at p comes from p - r.
+PATH_DIRS = [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, 1), (1, -1), (-1, -1)]
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library next to it (gcc, -O2)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            I = ctypes.c_int
+            Dd = ctypes.c_double
+            lib.oracle_census.argtypes = [P, I, I, I, I, P]
+            lib.oracle_cost.argtypes = [P, P, I, I, I, I, P]
+            lib.oracle_path.argtypes = [P, I, I, I, I, I, I, I, P]
+            lib.oracle_aggregate.argtypes = [P, I, I, I, I, I, I, P]
+            lib.oracle_select.argtypes = [P, I, I, I, I, I, I, Dd, P, P, P, P]
+            lib.oracle_compute.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, I, Dd, Dd,
+                                           P, P, P, P, P, P, P]
+            for fn in ("oracle_census", "oracle_cost", "oracle_path", "oracle_aggregate",
+                       "oracle_select", "oracle_compute"):
+                getattr(lib, fn).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with status {rc}")
+
+
+def census(img: np.ndarray, ww: int, wh: int) -> np.ndarray:
+    """Census codes (uint64, H x W) of one uint8 view."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    out = np.empty((H, W), dtype=np.uint64)
+    _check(_load().oracle_census(_ptr(img), W, H, ww, wh, _ptr(out)), "census")
+    return out
+
+
+def cost(cl: np.ndarray, cr: np.ndarray, D: int, nbits: int) -> np.ndarray:
+    """Hamming cost volume C (uint8, H x W x D)."""
+    cl = np.ascontiguousarray(cl, dtype=np.uint64)
+    cr = np.ascontiguousarray(cr, dtype=np.uint64)
+    H, W = cl.shape
+    out = np.empty((H, W, D), dtype=np.uint8)
+    _check(_load().oracle_cost(_ptr(cl), _ptr(cr), W, H, D, nbits, _ptr(out)), "cost")
+    return out
+
+
+def path(C: np.ndarray, rx: int, ry: int, P1: int, P2: int) -> np.ndarray:
+    """One SGM path L_r (int32, H x W x D) along r = (rx, ry)."""
+    C = np.ascontiguousarray(C, dtype=np.uint8)
+    H, W, D = C.shape
+    out = np.empty((H, W, D), dtype=np.int32)
+    _check(_load().oracle_path(_ptr(C), W, H, D, rx, ry, P1, P2, _ptr(out)), "path")
+    return out
+
+
+def aggregate(C: np.ndarray, paths: int, P1: int, P2: int) -> np.ndarray:
+    """Aggregated cost S = sum of the paths' L_r (int32, H x W x D)."""
+    C = np.ascontiguousarray(C, dtype=np.uint8)
+    H, W, D = C.shape
+    out = np.empty((H, W, D), dtype=np.int32)
+    _check(_load().oracle_aggregate(_ptr(C), W, H, D, paths, P1, P2, _ptr(out)), "aggregate")
+    return out
+
+
+def select(S: np.ndarray, uniq: int, lr_max_diff: int, subpixel: bool, fb: float):
+    """Selection and post-processing of an aggregated volume.
+
+    Returns (dstar int32, mask uint8, disp float64, depth float64), each H x W.
+    """
+    S = np.ascontiguousarray(S, dtype=np.int32)
+    H, W, D = S.shape
+    dstar = np.empty((H, W), dtype=np.int32)
+    mask = np.empty((H, W), dtype=np.uint8)
+    disp = np.empty((H, W), dtype=np.float64)
+    depth = np.empty((H, W), dtype=np.float64)
+    _check(_load().oracle_select(_ptr(S), W, H, D, uniq, lr_max_diff, int(bool(subpixel)), float(fb),
+                                 _ptr(dstar), _ptr(mask), _ptr(disp), _ptr(depth)), "select")
+    return dstar, mask, disp, depth
+
+
+def compute(left, right, D, ww, wh, P1, P2, paths, uniq, lr_max_diff, subpixel, f, baseline,
+            want_codes=False, want_S=False):
+    """The whole stage for one pair.  Returns a dict of numpy arrays.
+
+    ``f`` and ``baseline`` are converted to float32 first, as the library
+    receives them, and their product is then formed in fp64.
+    """
+    left = np.ascontiguousarray(left, dtype=np.uint8)
+    right = np.ascontiguousarray(right, dtype=np.uint8)
+    H, W = left.shape
+    f32 = float(np.float32(f))
+    b32 = float(np.float32(baseline))
+    out = {
+        "depth": np.empty((H, W), dtype=np.float64),
+        "disp": np.empty((H, W), dtype=np.float64),
+        "dstar": np.empty((H, W), dtype=np.int32),
+        "mask": np.empty((H, W), dtype=np.uint8),
+    }
+    cl = np.empty((H, W), dtype=np.uint64) if want_codes else None
+    cr = np.empty((H, W), dtype=np.uint64) if want_codes else None
+    S = np.empty((H, W, D), dtype=np.int32) if want_S else None
+    rc = _load().oracle_compute(_ptr(left), _ptr(right), W, H, D, ww, wh, P1, P2, paths, uniq,
+                                lr_max_diff, int(bool(subpixel)), f32, b32,
+                                _ptr(out["depth"]), _ptr(out["disp"]), _ptr(out["dstar"]),
+                                _ptr(out["mask"]), _ptr(cl), _ptr(cr), _ptr(S))
+    _check(rc, "compute")
+    if want_codes:
+        out["codes_left"], out["codes_right"] = cl, cr
+    if want_S:
+        out["S"] = S
+    return out

@@ -1,0 +1,281 @@
+/*
+ * Plain CPU oracle for the depth-estimation stage of an active-stereo
+ * sensor simulator (arxiv 2201.11924, Sec. VI-D "Depth Generation by Stereo
+ * Matching").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: it exists so that the tests, the smoke check and the CPU
+ * baseline leg of the benchmark can compare the CUDA library against a slow,
+ * obviously correct restatement of the method.  It shares no code, header,
+ * table or helper with the CUDA sources.
+ *
+ * Sec. VI-D fixes the order of the steps: census transform, Hamming matching
+ * cost, semi-global matching (SGM) cost aggregation along scanline paths,
+ * best-disparity selection with a uniqueness test, quadratic sub-pixel
+ * fitting, a left-right consistency check, and conversion of disparity to
+ * depth.  Each function below is one step, written as plain nested loops in
+ * int32 arithmetic (floating point only in the sub-pixel and depth steps,
+ * where it is fp64).  There is no blocking, fusion or reordering.
+ *
+ * Readings of points the paper leaves open (all of them are listed in the
+ * design notes of the repository):
+ *  - census: full census over a w x h window without its centre,
+ *    bit = [I(neighbour) < I(centre)], neighbours outside the image give 0,
+ *    bits in raster order (dy outer, dx inner), first offset = most
+ *    significant bit.  (Sec. VI-D names a centre-symmetric census; the
+ *    bit counts of the configured windows, 24 / 48 / 62, are those of the
+ *    full census.)
+ *  - cost: C(x,y,d) = popcount(cL(x,y) xor cR(x-d,y)) when x-d >= 0, else
+ *    nbits (the worst possible cost); d runs over 0..D-1.
+ *  - SGM (Hirschmueller's recurrence, which Sec. VI-D cites):
+ *      L_r(p,d) = C(p,d) + min(L'(d), L'(d-1)+P1, L'(d+1)+P1, m'+P2) - m'
+ *    with L' = L_r(p-r, .), m' = min_k L'(k), L'(-1) = L'(D) = +inf, and
+ *    L_r(p,d) = C(p,d) where p-r is outside the image.  S = sum_r L_r.
+ *    4 paths = {->, <-, down, up}; 8 paths add the four diagonals.
+ *  - selection: d* = argmin_d S (smallest d on ties); uniqueness with an
+ *    integer percentage u: unique iff for all d with |d-d*| > 1,
+ *    (100-u) S(d) >= 100 S(d*)  (u = 0 disables it).
+ *  - left-right check: D_R(xr) = argmin over d in [0, min(D-1, W-1-xr)] of
+ *    S(xr+d, y, d) (smallest d on ties); valid iff x-d* >= 0 and
+ *    |d* - D_R(x-d*)| <= lr_max_diff (lr_max_diff < 0 disables it).
+ *  - sub-pixel: for 1 <= d* <= D-2, d_f = d* + (S- - S+) / (2 (S- + S+ - 2 S0)),
+ *    else d_f = d*;  the checks above use the integer d*.
+ *  - depth: Z = f b / d_f for a valid pixel with d_f > 0, else 0.
+ *  - mask bits: 1 = uniqueness failed, 2 = left-right failed,
+ *    4 = d_f <= 0.  A pixel is valid iff its mask is 0.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_OK 0
+#define ORACLE_BAD_ARG -1
+#define ORACLE_NO_MEMORY -2
+
+/* ---------------------------------------------------------------- census */
+
+/* Census transform of one view (Sec. VI-D, first step after rectification).
+ * img: H x W bytes, row-major.  codes: H x W uint64, row-major. */
+int oracle_census(const uint8_t* img, int W, int H, int ww, int wh, uint64_t* codes)
+{
+    if (!img || !codes || W <= 0 || H <= 0) return ORACLE_BAD_ARG;
+    if (ww < 1 || wh < 1 || (ww % 2) == 0 || (wh % 2) == 0) return ORACLE_BAD_ARG;
+    if (ww * wh - 1 > 64) return ORACLE_BAD_ARG;
+    int rx = ww / 2, ry = wh / 2;
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            int centre = img[y * W + x];
+            uint64_t code = 0;
+            for (int dy = -ry; dy <= ry; dy++) {
+                for (int dx = -rx; dx <= rx; dx++) {
+                    if (dx == 0 && dy == 0) continue;
+                    int nx = x + dx, ny = y + dy;
+                    int bit = 0;
+                    if (nx >= 0 && nx < W && ny >= 0 && ny < H)
+                        bit = img[ny * W + nx] < centre ? 1 : 0;
+                    /* shifting before each new bit leaves the first offset in
+                     * the most significant used position */
+                    code = (code << 1) | (uint64_t)bit;
+                }
+            }
+            codes[y * W + x] = code;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* ----------------------------------------------------------- matching cost */
+
+static int hamming64(uint64_t a, uint64_t b)
+{
+    uint64_t v = a ^ b;
+    int n = 0;
+    for (int k = 0; k < 64; k++) n += (int)((v >> k) & 1u);
+    return n;
+}
+
+/* Hamming matching cost volume (Sec. VI-D: "hamming distance as the cost
+ * function").  C: H x W x D bytes, index (y*W + x)*D + d. */
+int oracle_cost(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int nbits, uint8_t* C)
+{
+    if (!cL || !cR || !C || W <= 0 || H <= 0 || D <= 0 || nbits < 0 || nbits > 64) return ORACLE_BAD_ARG;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++)
+            for (int d = 0; d < D; d++) {
+                int c = nbits;
+                if (x - d >= 0) c = hamming64(cL[y * W + x], cR[y * W + (x - d)]);
+                C[((size_t)y * W + x) * D + d] = (uint8_t)c;
+            }
+    return ORACLE_OK;
+}
+
+/* --------------------------------------------------------------------- SGM */
+
+/* One SGM path (Hirschmueller's recurrence, the SGM that Sec. VI-D cites),
+ * along direction r = (rx, ry): the value at p comes from p - r.
+ * L: H x W x D int32, index (y*W + x)*D + d. */
+int oracle_path(const uint8_t* C, int W, int H, int D, int rx, int ry, int P1, int P2, int32_t* L)
+{
+    if (!C || !L || W <= 0 || H <= 0 || D <= 0) return ORACLE_BAD_ARG;
+    if (rx < -1 || rx > 1 || ry < -1 || ry > 1 || (rx == 0 && ry == 0)) return ORACLE_BAD_ARG;
+    if (P1 < 0 || P2 < P1) return ORACLE_BAD_ARG;
+    /* visit pixels so that p - r is always visited before p */
+    int y0 = ry >= 0 ? 0 : H - 1, y1 = ry >= 0 ? H : -1, ys = ry >= 0 ? 1 : -1;
+    int x0 = rx >= 0 ? 0 : W - 1, x1 = rx >= 0 ? W : -1, xs = rx >= 0 ? 1 : -1;
+    for (int y = y0; y != y1; y += ys) {
+        for (int x = x0; x != x1; x += xs) {
+            const uint8_t* c = C + ((size_t)y * W + x) * D;
+            int32_t* l = L + ((size_t)y * W + x) * D;
+            int qx = x - rx, qy = y - ry;
+            if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+                for (int d = 0; d < D; d++) l[d] = c[d];
+                continue;
+            }
+            const int32_t* lp = L + ((size_t)qy * W + qx) * D;
+            int32_t mprev = lp[0];
+            for (int k = 1; k < D; k++)
+                if (lp[k] < mprev) mprev = lp[k];
+            for (int d = 0; d < D; d++) {
+                int32_t best = lp[d];
+                if (d - 1 >= 0 && lp[d - 1] + P1 < best) best = lp[d - 1] + P1;
+                if (d + 1 < D && lp[d + 1] + P1 < best) best = lp[d + 1] + P1;
+                if (mprev + P2 < best) best = mprev + P2;
+                l[d] = (int32_t)c[d] + best - mprev;
+            }
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* The path set: 4 paths = {->, <-, down, up}; 8 paths add the diagonals. */
+static const int PATH_DIRS[8][2] = {
+    {1, 0}, {-1, 0}, {0, 1}, {0, -1},
+    {1, 1}, {-1, 1}, {1, -1}, {-1, -1},
+};
+
+/* Aggregated cost S = sum over the paths of L_r.  S: H x W x D int32. */
+int oracle_aggregate(const uint8_t* C, int W, int H, int D, int paths, int P1, int P2, int32_t* S)
+{
+    if (!C || !S || W <= 0 || H <= 0 || D <= 0) return ORACLE_BAD_ARG;
+    if (paths != 4 && paths != 8) return ORACLE_BAD_ARG;
+    size_t n = (size_t)W * H * D;
+    int32_t* L = (int32_t*)malloc(n * sizeof(int32_t));
+    if (!L) return ORACLE_NO_MEMORY;
+    memset(S, 0, n * sizeof(int32_t));
+    for (int r = 0; r < paths; r++) {
+        int rc = oracle_path(C, W, H, D, PATH_DIRS[r][0], PATH_DIRS[r][1], P1, P2, L);
+        if (rc != ORACLE_OK) { free(L); return rc; }
+        for (size_t i = 0; i < n; i++) S[i] += L[i];
+    }
+    free(L);
+    return ORACLE_OK;
+}
+
+/* Direction vector of path index r (0..7), for callers that dump one path. */
+int oracle_path_dir(int r, int* rx, int* ry)
+{
+    if (r < 0 || r > 7 || !rx || !ry) return ORACLE_BAD_ARG;
+    *rx = PATH_DIRS[r][0];
+    *ry = PATH_DIRS[r][1];
+    return ORACLE_OK;
+}
+
+/* -------------------------------------------- selection and post-processing */
+
+/* Best disparity, uniqueness test, left-right check, quadratic sub-pixel fit
+ * and disparity-to-depth conversion (the remaining steps of Sec. VI-D).
+ * S: H x W x D int32.  Outputs are H x W; any output pointer may be NULL
+ * except dstar.  fb = focal length (px) times baseline (m). */
+int oracle_select(const int32_t* S, int W, int H, int D, int uniq, int lr_max_diff,
+                  int subpixel, double fb, int32_t* dstar, uint8_t* mask,
+                  double* disp, double* depth)
+{
+    if (!S || !dstar || W <= 0 || H <= 0 || D <= 0 || uniq < 0 || uniq > 99) return ORACLE_BAD_ARG;
+    /* pass 1: winner-take-all for every pixel */
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            const int32_t* s = S + ((size_t)y * W + x) * D;
+            int best = 0;
+            for (int d = 1; d < D; d++)
+                if (s[d] < s[best]) best = d;
+            dstar[y * W + x] = best;
+        }
+    /* pass 2: checks, sub-pixel, depth */
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            const int32_t* s = S + ((size_t)y * W + x) * D;
+            int ds = dstar[y * W + x];
+            int m = 0;
+            if (uniq > 0) {
+                for (int d = 0; d < D; d++) {
+                    int diff = d - ds;
+                    if (diff < 0) diff = -diff;
+                    if (diff <= 1) continue;
+                    if ((int64_t)(100 - uniq) * s[d] < (int64_t)100 * s[ds]) { m |= 1; break; }
+                }
+            }
+            if (lr_max_diff >= 0) {
+                int xr = x - ds;
+                if (xr < 0) {
+                    m |= 2;
+                } else {
+                    int dmax = D - 1;
+                    if (W - 1 - xr < dmax) dmax = W - 1 - xr;
+                    int dr = 0;
+                    int32_t sbest = S[((size_t)y * W + xr) * D + 0];
+                    for (int d = 1; d <= dmax; d++) {
+                        int32_t v = S[((size_t)y * W + (xr + d)) * D + d];
+                        if (v < sbest) { sbest = v; dr = d; }
+                    }
+                    int diff = ds - dr;
+                    if (diff < 0) diff = -diff;
+                    if (diff > lr_max_diff) m |= 2;
+                }
+            }
+            double df = (double)ds;
+            if (subpixel && ds >= 1 && ds <= D - 2) {
+                double sm = s[ds - 1], s0 = s[ds], sp = s[ds + 1];
+                df = (double)ds + (sm - sp) / (2.0 * (sm + sp - 2.0 * s0));
+            }
+            if (!(df > 0.0)) m |= 4;
+            if (mask) mask[y * W + x] = (uint8_t)m;
+            if (disp) disp[y * W + x] = m == 0 ? df : -1.0;
+            if (depth) depth[y * W + x] = m == 0 ? fb / df : 0.0;
+        }
+    return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------ whole stage */
+
+/* The whole depth stage for one rectified pair.  Every output except depth
+ * may be NULL.  codes: H x W; cost: H x W x D bytes; S: H x W x D int32. */
+int oracle_compute(const uint8_t* left, const uint8_t* right, int W, int H, int D,
+                   int ww, int wh, int P1, int P2, int paths, int uniq, int lr_max_diff,
+                   int subpixel, double f, double baseline,
+                   double* depth, double* disp, int32_t* dstar, uint8_t* mask,
+                   uint64_t* codes_left, uint64_t* codes_right, int32_t* S_out)
+{
+    if (!left || !right || !depth || W <= 0 || H <= 0 || D <= 0) return ORACLE_BAD_ARG;
+    int nbits = ww * wh - 1;
+    size_t npx = (size_t)W * H, nvol = npx * (size_t)D;
+    uint64_t* cl = codes_left ? codes_left : (uint64_t*)malloc(npx * sizeof(uint64_t));
+    uint64_t* cr = codes_right ? codes_right : (uint64_t*)malloc(npx * sizeof(uint64_t));
+    uint8_t* C = (uint8_t*)malloc(nvol);
+    int32_t* S = S_out ? S_out : (int32_t*)malloc(nvol * sizeof(int32_t));
+    int32_t* ds = dstar ? dstar : (int32_t*)malloc(npx * sizeof(int32_t));
+    int rc = ORACLE_OK;
+    if (!cl || !cr || !C || !S || !ds) { rc = ORACLE_NO_MEMORY; goto done; }
+    rc = oracle_census(left, W, H, ww, wh, cl);
+    if (rc == ORACLE_OK) rc = oracle_census(right, W, H, ww, wh, cr);
+    if (rc == ORACLE_OK) rc = oracle_cost(cl, cr, W, H, D, nbits, C);
+    if (rc == ORACLE_OK) rc = oracle_aggregate(C, W, H, D, paths, P1, P2, S);
+    if (rc == ORACLE_OK)
+        rc = oracle_select(S, W, H, D, uniq, lr_max_diff, subpixel, f * baseline, ds, mask, disp, depth);
+done:
+    if (!codes_left) free(cl);
+    if (!codes_right) free(cr);
+    free(C);
+    if (!S_out) free(S);
+    if (!dstar) free(ds);
+    return rc;
+}
