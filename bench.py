@@ -1,0 +1,350 @@
+"""Benchmark of the GB300 depth stage: depth frames/s on the 1280x720, D=128,
+7x7-census, 8-path workload (one rectified pair per step, plain path).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints ONE JSON line (rank 0).  ``value`` is device-timed whole-job
+throughput with the inputs resident in HBM; ``e2e`` is the same metric
+through the host-buffer C-ABI call (pinned host -> device copies, compute,
+depth copied back, every step); ``roofline`` reports the dominant kernel's
+achieved integer-op rate (algorithmic ops / its CUDA-event duration) against
+the derived INT32 peak; ``cpu_baseline`` is the CPU oracle timed on a bounded
+sample on this host.  ``--impl reference`` times that oracle alone, on the
+same workload and metric (the paper's own SimSense implementation is not
+public code, so the oracle is the reference arm).
+
+Under torchrun each rank runs an independent replica on its own GPU (pairs
+are independent; no data-path collective); the value divides all ranks'
+frames by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import datetime
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2201_11924_gb300 import configs, scenes  # noqa: E402
+
+METRIC = "depth_frames_per_s"
+UNIT = "frames/s"
+N_SM_NOMINAL = 152
+INT32_LANES_PER_SM = 128          # INT32 results per clock per SM
+SM_MAX_MHZ = 2070.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+def algorithmic_ops(wl):
+    """Scalar integer ops per launch of each kernel (no SIMD credit).
+
+    Per cell (x, y, d): the Hamming cost once (XOR, POPC on 64-bit codes:
+    5 ops; on 32-bit codes: 2), 7 ops per path for the recurrence (min of the
+    neighbours, +P1, min with L'(d), -m', min with P2, +C, the min-reduction
+    over d), then in the selection kernel the sum over the paths (1 per path)
+    and 6 for WTA, uniqueness and the right-view argmin.  The census costs
+    2 ops per bit per view and pixel."""
+    cells = wl.W * wl.H * wl.D
+    cost = 5 if wl.nbits > 32 else 2
+    return {
+        "paths": cells * (cost + 7 * wl.paths),
+        "select": cells * (wl.paths + 6),
+        "census": wl.W * wl.H * 4 * wl.nbits,
+    }
+
+
+def algorithmic_bytes(wl):
+    """HBM bytes per frame the method must move: both views in (2 B/px),
+    depth out (4 B/px) and one spilled partial-sum volume between the forward
+    and backward path sweeps (uint16 for 8 paths, 2 B written + 2 B read per
+    cell; uint8 for 4 paths)."""
+    spill = 4 if wl.paths == 8 else 2
+    return 6 * wl.W * wl.H + spill * wl.W * wl.H * wl.D
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.proc = None
+        self.path = None
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = [exe, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if bus_id:
+            cmd += ["-i", bus_id]
+        self.fh = open(self.path, "w")
+        self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        t0 = time.time()
+        while time.time() - t0 < 5.0:           # wait for the first sample
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
+
+    def stop(self, t0, t1):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    rows.append((ts, float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        inside = [r for r in rows if t0 - 0.05 <= r[0] <= t1 + 0.05] or rows[-3:]
+        if not inside:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in inside for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[1] for r in inside), "sm_max_mhz": max(r[2] for r in inside),
+                "reasons": reasons, "samples": len(inside)}
+
+
+def _bus_id(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+    except Exception:
+        return None
+
+
+def cpu_oracle_rate(wl, pair, budget_s=10.0, strip_rows=90):
+    """Oracle cells/s on full-width horizontal strips of the pair (each strip
+    is a complete W x strip_rows problem: same per-cell work as the frame)."""
+    import oracle
+    cells = 0
+    t0 = time.perf_counter()
+    n = 0
+    H = wl.H
+    while True:
+        y0 = (n * strip_rows) % max(1, H - strip_rows + 1)
+        l = pair["left"][y0:y0 + strip_rows]
+        r = pair["right"][y0:y0 + strip_rows]
+        oracle.compute(l, r, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq,
+                       wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline)
+        cells += wl.W * l.shape[0] * wl.D
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s:
+            break
+    return cells / el, n, el
+
+
+def run_reference(args, wl):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    pair = scenes.make_pair(wl)
+    strip = args.ref_strip_rows
+    import oracle
+    oracle.build()
+
+    def step(i):
+        y0 = (i * strip) % max(1, wl.H - strip + 1)
+        oracle.compute(pair["left"][y0:y0 + strip], pair["right"][y0:y0 + strip], wl.D, wl.win_w, wl.win_h,
+                       wl.P1, wl.P2, wl.paths, wl.uniq, wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(i)
+    el = time.perf_counter() - t0
+    cells = args.steps * wl.W * strip * wl.D
+    value = cells / el / wl.cells
+    sample = f"{wl.W}x{strip} full-width strip of the {wl.W}x{wl.H} pair per step, per-cell rate extrapolated to frames"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "W": wl.W, "H": wl.H, "D": wl.D, "paths": wl.paths,
+                   "census": f"{wl.win_w}x{wl.win_h}"},
+        "cells_per_s": cells / el,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="simsense", choices=["simsense", "reference"])
+    ap.add_argument("--workload", default=configs.HD_720.name, choices=sorted(configs.ALL))
+    ap.add_argument("--cpu-budget-s", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-strip-rows", type=int, default=90)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = configs.ALL[args.workload]
+
+    if args.impl == "reference":
+        return run_reference(args, wl)
+
+    import torch
+    from paper_2201_11924_gb300 import simsense
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    # a few distinct seeded pairs per rank, resident in HBM
+    n_pairs = 4
+    pairs = [scenes.make_pair(wl, seed=wl.seed + 1000 * rank + i) for i in range(n_pairs)]
+    lefts = [torch.from_numpy(p["left"]).to(dev) for p in pairs]
+    rights = [torch.from_numpy(p["right"]).to(dev) for p in pairs]
+    depth = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+    m = simsense.SimSense.from_workload(wl)
+    stream = torch.cuda.current_stream(dev)
+
+    for i in range(args.warmup):
+        m.compute(lefts[i % n_pairs], rights[i % n_pairs], depth)
+    torch.cuda.synchronize()
+    m.set_option(simsense.OPT_PROFILE, 1)
+
+    sampler = ClockSampler(_bus_id(torch, dev))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        m.compute(lefts[i % n_pairs], rights[i % n_pairs], depth)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall1 = time.time()
+    clocks = sampler.stop(t_wall0, t_wall1)
+    el_ms = ev0.elapsed_time(ev1)
+    stage_ms, n_prof = m.profile_read()
+    m.set_option(simsense.OPT_PROFILE, 0)
+    if dist:
+        t = torch.tensor([el_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+    value = world * args.steps / (el_ms / 1e3)
+
+    # end to end through the host-buffer call: pinned inputs in, depth out
+    hl = [torch.from_numpy(p["left"]).pin_memory() for p in pairs]
+    hr = [torch.from_numpy(p["right"]).pin_memory() for p in pairs]
+    hd = torch.empty((wl.H, wl.W), dtype=torch.float32).pin_memory()
+    for i in range(args.warmup):
+        m.compute_host(hl[i % n_pairs], hr[i % n_pairs], hd)
+        stream.synchronize()
+    if dist:
+        dist.barrier()
+    e2e_steps = max(3, min(args.steps, 500))
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        m.compute_host(hl[i % n_pairs], hr[i % n_pairs], hd)
+        stream.synchronize()
+        _ = float(hd[0, 0])
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * wl.W * wl.H, "d2h_bytes_per_step": 4 * wl.W * wl.H,
+           "steps": e2e_steps}
+
+    if rank != 0:
+        m.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel, from the live stage events
+    ops = algorithmic_ops(wl)
+    dom = max(stage_ms, key=stage_ms.get)
+    launch_s = stage_ms[dom] / 1e3 / max(1, n_prof)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
+    int_peak = n_sm * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12        # T ops/s
+    achieved = ops[dom] / launch_s / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": int_peak,
+                "unit": "Tops/s", "frac": achieved / int_peak, "traffic": None,
+                "peak_source": f"derived: {n_sm} SMs x {INT32_LANES_PER_SM} INT32 lanes x {sm_max:.0f} MHz",
+                "stage_ms_per_step": {k: v / max(1, n_prof) for k, v in stage_ms.items()},
+                "hbm_algorithmic_bytes_per_frame": algorithmic_bytes(wl),
+                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rate, n, el = cpu_oracle_rate(wl, pairs[0], budget_s=args.cpu_budget_s)
+        cpu = {"value": rate / wl.cells, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{n} full-width {wl.W}x90 strips of one pair ({el:.1f} s), per-cell rate extrapolated"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": wl.name, "W": wl.W, "H": wl.H, "D": wl.D, "paths": wl.paths,
+                   "census": f"{wl.win_w}x{wl.win_h}", "P1": wl.P1, "P2": wl.P2, "uniq": wl.uniq,
+                   "lr_max_diff": wl.lr_max_diff, "subpixel": wl.subpixel, "pairs_cycled": n_pairs,
+                   "l2": "no flush: every step streams its own ~1 GB path volume through HBM, "
+                         "far above the 129 MB L2", "path": "plain (one pair per call)"},
+        "cells_per_s": value * wl.cells,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    m.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

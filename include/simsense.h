@@ -1,0 +1,179 @@
+/*
+ * simsense.h — C ABI of the GB300 (sm_103a) depth stage of an active-stereo
+ * sensor simulator: rectified left/right IR pair in, depth map out.
+ *
+ * The stage follows arxiv 2201.11924, Sec. VI-D ("Depth Generation by Stereo
+ * Matching"): census transform of both views, Hamming matching cost, semi-
+ * global matching (SGM) cost aggregation along 4 or 8 scanline paths with
+ * penalties P1/P2, winner-take-all with a uniqueness test, a left-right
+ * consistency check, quadratic (parabolic) sub-pixel refinement and the
+ * conversion of disparity d to depth Z = f * b / d.  Sec. VI-D also states
+ * that the module's key parameters are adjustable per sensor; they are the
+ * arguments of simsense_create().
+ *
+ * Definitions (the readings of points the paper leaves open):
+ *  - census over a w x h window without its centre, bit = [I(nbr) < I(ctr)],
+ *    neighbours outside the image give 0, bits in raster order with the first
+ *    offset as the most significant bit; nbits = w*h - 1.
+ *  - cost C(x,y,d) = popcount(cL(x,y) ^ cR(x-d,y)) for x-d >= 0, else nbits;
+ *    d = 0 .. D-1.
+ *  - SGM: L_r(p,d) = C(p,d) + min(L'(d), L'(d+-1)+P1, m'+P2) - m' with
+ *    L' = L_r(p-r,.), m' = min L'; L_r = C where p-r is outside the image;
+ *    S = sum over the paths of L_r.  4 paths: -> <- down up; 8 paths add the
+ *    diagonals.
+ *  - d* = argmin_d S (smallest d on ties).  Uniqueness (u = uniq_ratio in
+ *    percent, 0 disables): unique iff (100-u) S(d) >= 100 S(d*) for every d
+ *    with |d-d*| > 1.
+ *  - left-right check (lr_max_diff < 0 disables): D_R(xr) = argmin over
+ *    d <= min(D-1, W-1-xr) of S(xr+d, y, d) (smallest d on ties); the pixel
+ *    passes iff x-d* >= 0 and |d* - D_R(x-d*)| <= lr_max_diff.
+ *  - sub-pixel (on by default): for 1 <= d* <= D-2,
+ *    d_f = d* + (S- - S+) / (2 (S- + S+ - 2 S0)) in IEEE fp32 (one
+ *    round-to-nearest division of the two exact integers), else d_f = d*.
+ *  - depth: Z = fb / d_f (fp32, round to nearest) with fb = (float)(f * b)
+ *    formed in double; Z = 0 for a pixel that failed a check or has d_f <= 0.
+ *
+ * Conventions for every call:
+ *  - images are contiguous row-major with pitch W (no padding): uint8 H x W
+ *    for the views, float32 H x W for depth; caller-owned; inputs and outputs
+ *    must not overlap.
+ *  - the library owns its scratch memory: it is allocated by simsense_create
+ *    and released by simsense_destroy; simsense_compute allocates nothing.
+ *  - compute calls are asynchronous on the given CUDA stream (NULL = the
+ *    legacy default stream); results are ready once the stream has been
+ *    synchronised.  One handle must not be used by two streams at once (its
+ *    scratch is shared by its calls).
+ *  - every call returns a status code (SIMSENSE_OK or a negative error);
+ *    nothing aborts, traps or prints.  simsense_last_cuda_error() returns the
+ *    CUDA error code behind the most recent SIMSENSE_ERR_CUDA of a handle.
+ */
+#ifndef SIMSENSE_H
+#define SIMSENSE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;                       /* = cudaStream_t */
+typedef struct simsense_ctx* simsense_t;
+
+/* status codes */
+#define SIMSENSE_OK                 0
+#define SIMSENSE_ERR_INVALID_ARG   -1     /* an argument is out of range or NULL */
+#define SIMSENSE_ERR_OOM           -2     /* scratch allocation failed */
+#define SIMSENSE_ERR_CUDA          -3     /* a CUDA call or launch failed */
+#define SIMSENSE_ERR_TIMEOUT       -4     /* a bounded device-side wait gave up */
+
+/* options for simsense_set_option */
+#define SIMSENSE_OPT_SUBPIXEL       1     /* value 0/1, default 1 */
+#define SIMSENSE_OPT_PROFILE        2     /* value 0/1, default 0: time each stage */
+
+/* stages timed under SIMSENSE_OPT_PROFILE, in launch order */
+#define SIMSENSE_STAGE_CENSUS       0     /* census transform of both views */
+#define SIMSENSE_STAGE_PATHS        1     /* matching cost + SGM path aggregation */
+#define SIMSENSE_STAGE_SELECT       2     /* sum of paths, WTA, checks, sub-pixel, depth */
+#define SIMSENSE_NUM_STAGES         3
+
+/* census_win packs the window as w | (h << 8); h = 0 means a square w x w. */
+#define SIMSENSE_WIN(w, h) ((w) | ((h) << 8))
+
+/*
+ * Create a matcher for W x H pairs with disparities 0 .. D-1 (Sec. VI-D:
+ * the stage's adjustable parameters).
+ *   census_win   SIMSENSE_WIN(w, h) with odd w, h and w*h - 1 <= 64
+ *                (e.g. 5x5 -> 24 bits, 7x7 -> 48, 9x7 -> 62)
+ *   P1, P2       SGM penalties, 0 <= P1 <= P2 and nbits + P2 <= 255
+ *   paths        4 or 8
+ *   uniq_ratio   0 .. 99 (percent; 0 disables the uniqueness test)
+ *   lr_max_diff  < 0 disables the left-right check
+ *   f, baseline  focal length in pixels and baseline in metres, both > 0
+ * Limits: 1 <= D <= 256, D <= W, w <= W <= 16384 and h <= H <= 16384.
+ * Returns SIMSENSE_ERR_INVALID_ARG for anything outside these ranges,
+ * SIMSENSE_ERR_OOM if the scratch memory cannot be allocated on the current
+ * device (the handle is bound to that device).  On success *out owns the
+ * handle; release it with simsense_destroy.
+ */
+int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1, int P2,
+                    int paths, int uniq_ratio, int lr_max_diff, float f, float baseline);
+
+/*
+ * Depth of one rectified pair (the whole of Sec. VI-D after rectification).
+ *   left_u8, right_u8   device pointers, H x W uint8
+ *   depth_f32           device pointer, H x W float32 (written in full)
+ *   stream              CUDA stream the kernels are enqueued on
+ */
+int simsense_compute(simsense_t h, const uint8_t* left_u8, const uint8_t* right_u8,
+                     float* depth_f32, struct CUstream_st* stream);
+
+/*
+ * Same as simsense_compute for HOST buffers: copies both views from host
+ * memory into the handle's device staging buffers, runs the stage and copies
+ * the depth map back, all enqueued on stream.  Page-locked host buffers make
+ * the copies asynchronous; with pageable ones the copies block the host.
+ * The depth buffer is complete once the stream has been synchronised.
+ */
+int simsense_compute_host(simsense_t h, const uint8_t* left_host, const uint8_t* right_host,
+                          float* depth_host, struct CUstream_st* stream);
+
+/*
+ * Intermediate results of one compute call, all DEVICE pointers; any member
+ * may be NULL to skip it.  They are written by the same kernels that run in
+ * simsense_compute (no separate code path).
+ *   census_left/right  H x W uint64 codes (always widened to 64 bits)
+ *   aggregated         H x W x D uint16, S(x, y, d) at (y*W + x)*D + d
+ *   disparity_int      H x W int16, the winner d*
+ *   disparity          H x W float32, d_f of a valid pixel, -1.0f otherwise
+ *   mask               H x W uint8, bit 1 = uniqueness failed,
+ *                      bit 2 = left-right check failed, bit 4 = d_f <= 0
+ */
+typedef struct simsense_debug {
+    uint64_t* census_left;
+    uint64_t* census_right;
+    uint16_t* aggregated;
+    int16_t* disparity_int;
+    float* disparity;
+    uint8_t* mask;
+} simsense_debug_t;
+
+/* simsense_compute plus the intermediate results named in *dbg (device
+ * pointers, see simsense_debug_t).  dbg may be NULL. */
+int simsense_compute_debug(simsense_t h, const uint8_t* left_u8, const uint8_t* right_u8,
+                           float* depth_f32, const simsense_debug_t* dbg,
+                           struct CUstream_st* stream);
+
+/* Set an option (SIMSENSE_OPT_*).  Takes effect at the next compute call. */
+int simsense_set_option(simsense_t h, int opt, int value);
+
+/*
+ * Stage timings.  While SIMSENSE_OPT_PROFILE is 1, every compute call records
+ * CUDA events around each stage on its stream (up to 4096 calls are kept).
+ * simsense_profile_read waits for the recorded events, writes into
+ * stage_ms[0 .. SIMSENSE_NUM_STAGES-1] the summed duration of each stage over
+ * the recorded calls, sets *n_calls to their number and clears the record.
+ * Either pointer may be NULL.
+ */
+int simsense_profile_read(simsense_t h, double* stage_ms, int* n_calls);
+
+/* Name of stage i (SIMSENSE_STAGE_*), or NULL. */
+const char* simsense_stage_name(int i);
+
+/* Bytes of device scratch memory the handle holds (for admission control). */
+size_t simsense_scratch_bytes(simsense_t h);
+
+/* Release the handle and its scratch memory.  NULL is accepted. */
+int simsense_destroy(simsense_t h);
+
+/* Static description of a status code. */
+const char* simsense_strerror(int code);
+
+/* CUDA error code (cudaError_t) behind the handle's last SIMSENSE_ERR_CUDA. */
+int simsense_last_cuda_error(simsense_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SIMSENSE_H */

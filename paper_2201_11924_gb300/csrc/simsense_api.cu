@@ -1,0 +1,289 @@
+// C ABI of libsimsense (declared in include/simsense.h): argument checks,
+// scratch ownership and the launch sequence census -> paths -> select.
+#include <math.h>
+#include <new>
+
+#include "internal.h"
+
+using namespace simsense;
+
+namespace {
+
+// Makes the handle's device current for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { ok = false; return; }
+        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int cuda_fail(simsense_ctx* h, cudaError_t e)
+{
+    if (h) h->last_cuda_error = (int)e;
+    return SIMSENSE_ERR_CUDA;
+}
+
+void free_scratch(Scratch& s)
+{
+    cudaFree(s.codes_left);
+    cudaFree(s.codes_right);
+    cudaFree(s.paths);
+    cudaFree(s.stage_left);
+    cudaFree(s.stage_right);
+    cudaFree(s.stage_depth);
+    s = Scratch{};
+}
+
+void free_profile(ProfileRing& r)
+{
+    if (r.ev) {
+        for (int i = 0; i < ProfileRing::kSlots * 2 * SIMSENSE_NUM_STAGES; i++)
+            if (r.ev[i]) cudaEventDestroy(r.ev[i]);
+        delete[] r.ev;
+    }
+    r = ProfileRing{};
+}
+
+// Records the start (end = false) or end of `stage` for the current call.
+cudaError_t mark(simsense_ctx* h, int stage, bool end, cudaStream_t st)
+{
+    ProfileRing& r = h->prof;
+    if (!r.on || r.count >= ProfileRing::kSlots) return cudaSuccess;
+    return cudaEventRecord(r.ev[r.count * 2 * SIMSENSE_NUM_STAGES + 2 * stage + (end ? 1 : 0)], st);
+}
+
+int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth,
+        const simsense_debug_t* dbg, cudaStream_t st)
+{
+    const Params& p = h->p;
+    Scratch& s = h->s;
+    cudaError_t e = mark(h, SIMSENSE_STAGE_CENSUS, false, st);
+    if (e == cudaSuccess) e = launch_census(p, left, right, s.codes_left, s.codes_right, st);
+    if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_CENSUS, true, st);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    e = mark(h, SIMSENSE_STAGE_PATHS, false, st);
+    if (e == cudaSuccess) e = launch_paths(p, s.codes_left, s.codes_right, s.paths, st);
+    if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_PATHS, true, st);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    SelectDebug sd{};
+    if (dbg) {
+        sd.aggregated = dbg->aggregated;
+        sd.disparity_int = dbg->disparity_int;
+        sd.disparity = dbg->disparity;
+        sd.mask = dbg->mask;
+    }
+    e = mark(h, SIMSENSE_STAGE_SELECT, false, st);
+    if (e == cudaSuccess) e = launch_select(p, s.paths, depth, sd, st);
+    if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_SELECT, true, st);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    if (h->prof.on && h->prof.count < ProfileRing::kSlots) h->prof.count++;
+    if (dbg && dbg->census_left) {
+        e = launch_widen_codes(p, s.codes_left, dbg->census_left, st);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+    }
+    if (dbg && dbg->census_right) {
+        e = launch_widen_codes(p, s.codes_right, dbg->census_right, st);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+    }
+    return SIMSENSE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1, int P2,
+                    int paths, int uniq_ratio, int lr_max_diff, float f, float baseline)
+{
+    if (!out) return SIMSENSE_ERR_INVALID_ARG;
+    *out = nullptr;
+    const int ww = census_win & 0xff;
+    int wh = (census_win >> 8) & 0xff;
+    if (wh == 0) wh = ww;
+    if ((census_win >> 16) != 0) return SIMSENSE_ERR_INVALID_ARG;
+    if (ww < 1 || wh < 1 || ww > kMaxWin || wh > kMaxWin || !(ww & 1) || !(wh & 1))
+        return SIMSENSE_ERR_INVALID_ARG;
+    const int nbits = ww * wh - 1;
+    if (nbits < 1 || nbits > 64) return SIMSENSE_ERR_INVALID_ARG;
+    if (W < ww || H < wh || W > (1 << 14) || H > (1 << 14)) return SIMSENSE_ERR_INVALID_ARG;
+    if (D < 1 || D > kMaxD || D > W) return SIMSENSE_ERR_INVALID_ARG;
+    if (P1 < 0 || P2 < P1 || nbits + P2 > 255) return SIMSENSE_ERR_INVALID_ARG;
+    if (paths != 4 && paths != 8) return SIMSENSE_ERR_INVALID_ARG;
+    if (uniq_ratio < 0 || uniq_ratio > 99) return SIMSENSE_ERR_INVALID_ARG;
+    if (!(f > 0.0f) || !(baseline > 0.0f) || !isfinite(f) || !isfinite(baseline))
+        return SIMSENSE_ERR_INVALID_ARG;
+
+    simsense_ctx* h = new (std::nothrow) simsense_ctx();
+    if (!h) return SIMSENSE_ERR_OOM;
+    Params& p = h->p;
+    p.W = W; p.H = H; p.D = D;
+    p.win_w = ww; p.win_h = wh; p.nbits = nbits;
+    p.P1 = P1; p.P2 = P2; p.paths = paths;
+    p.uniq = uniq_ratio; p.lr_max_diff = lr_max_diff;
+    p.subpixel = 1;
+    p.f = f; p.baseline = baseline;
+    p.fb = (float)((double)f * (double)baseline);
+    p.dpt = 2 * ((D + 63) / 64);
+    p.Dp = 32 * p.dpt;
+    p.wide_codes = nbits > 32;
+    if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SIMSENSE_ERR_CUDA; }
+
+    const size_t npx = (size_t)W * H;
+    const size_t code_bytes = npx * (p.wide_codes ? 8 : 4);
+    const size_t vol_bytes = (size_t)paths * npx * p.Dp;
+    Scratch& s = h->s;
+    bool ok = cudaMalloc(&s.codes_left, code_bytes) == cudaSuccess &&
+              cudaMalloc(&s.codes_right, code_bytes) == cudaSuccess &&
+              cudaMalloc((void**)&s.paths, vol_bytes) == cudaSuccess &&
+              cudaMalloc((void**)&s.stage_left, npx) == cudaSuccess &&
+              cudaMalloc((void**)&s.stage_right, npx) == cudaSuccess &&
+              cudaMalloc((void**)&s.stage_depth, npx * sizeof(float)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();   // clear the sticky-free allocation error
+        free_scratch(s);
+        delete h;
+        return SIMSENSE_ERR_OOM;
+    }
+    s.bytes = 2 * code_bytes + vol_bytes + 2 * npx + npx * sizeof(float);
+    *out = h;
+    return SIMSENSE_OK;
+}
+
+int simsense_compute(simsense_t h, const uint8_t* left_u8, const uint8_t* right_u8, float* depth_f32,
+                     struct CUstream_st* stream)
+{
+    return simsense_compute_debug(h, left_u8, right_u8, depth_f32, nullptr, stream);
+}
+
+int simsense_compute_debug(simsense_t h, const uint8_t* left_u8, const uint8_t* right_u8,
+                           float* depth_f32, const simsense_debug_t* dbg, struct CUstream_st* stream)
+{
+    if (!h || !left_u8 || !right_u8 || !depth_f32) return SIMSENSE_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return cuda_fail(h, cudaGetLastError());
+    return run(h, left_u8, right_u8, depth_f32, dbg, (cudaStream_t)stream);
+}
+
+int simsense_compute_host(simsense_t h, const uint8_t* left_host, const uint8_t* right_host,
+                          float* depth_host, struct CUstream_st* stream)
+{
+    if (!h || !left_host || !right_host || !depth_host) return SIMSENSE_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return cuda_fail(h, cudaGetLastError());
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t npx = (size_t)h->p.W * h->p.H;
+    cudaError_t e = cudaMemcpyAsync(h->s.stage_left, left_host, npx, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->s.stage_right, right_host, npx, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    int rc = run(h, h->s.stage_left, h->s.stage_right, h->s.stage_depth, nullptr, st);
+    if (rc != SIMSENSE_OK) return rc;
+    e = cudaMemcpyAsync(depth_host, h->s.stage_depth, npx * sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return SIMSENSE_OK;
+}
+
+int simsense_set_option(simsense_t h, int opt, int value)
+{
+    if (!h) return SIMSENSE_ERR_INVALID_ARG;
+    switch (opt) {
+        case SIMSENSE_OPT_SUBPIXEL:
+            if (value != 0 && value != 1) return SIMSENSE_ERR_INVALID_ARG;
+            h->p.subpixel = value;
+            return SIMSENSE_OK;
+        case SIMSENSE_OPT_PROFILE: {
+            if (value != 0 && value != 1) return SIMSENSE_ERR_INVALID_ARG;
+            ProfileRing& r = h->prof;
+            if (value && !r.ev) {
+                DeviceGuard g(h->device);
+                const int n = ProfileRing::kSlots * 2 * SIMSENSE_NUM_STAGES;
+                r.ev = new (std::nothrow) cudaEvent_t[n]();
+                if (!r.ev) return SIMSENSE_ERR_OOM;
+                for (int i = 0; i < n; i++) {
+                    cudaError_t e = cudaEventCreate(&r.ev[i]);
+                    if (e != cudaSuccess) { free_profile(r); return cuda_fail(h, e); }
+                }
+            }
+            r.on = value != 0;
+            r.count = 0;
+            return SIMSENSE_OK;
+        }
+        default:
+            return SIMSENSE_ERR_INVALID_ARG;
+    }
+}
+
+int simsense_profile_read(simsense_t h, double* stage_ms, int* n_calls)
+{
+    if (!h) return SIMSENSE_ERR_INVALID_ARG;
+    ProfileRing& r = h->prof;
+    double tot[SIMSENSE_NUM_STAGES] = {0};
+    DeviceGuard g(h->device);
+    for (int c = 0; c < r.count; c++) {
+        for (int st = 0; st < SIMSENSE_NUM_STAGES; st++) {
+            cudaEvent_t a = r.ev[c * 2 * SIMSENSE_NUM_STAGES + 2 * st];
+            cudaEvent_t b = r.ev[c * 2 * SIMSENSE_NUM_STAGES + 2 * st + 1];
+            cudaError_t e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e != cudaSuccess) return cuda_fail(h, e);
+            tot[st] += ms;
+        }
+    }
+    if (stage_ms)
+        for (int st = 0; st < SIMSENSE_NUM_STAGES; st++) stage_ms[st] = tot[st];
+    if (n_calls) *n_calls = r.count;
+    r.count = 0;
+    return SIMSENSE_OK;
+}
+
+const char* simsense_stage_name(int i)
+{
+    switch (i) {
+        case SIMSENSE_STAGE_CENSUS: return "census";
+        case SIMSENSE_STAGE_PATHS: return "paths";
+        case SIMSENSE_STAGE_SELECT: return "select";
+        default: return nullptr;
+    }
+}
+
+size_t simsense_scratch_bytes(simsense_t h)
+{
+    return h ? h->s.bytes : 0;
+}
+
+int simsense_destroy(simsense_t h)
+{
+    if (!h) return SIMSENSE_OK;
+    DeviceGuard g(h->device);
+    free_scratch(h->s);
+    free_profile(h->prof);
+    delete h;
+    return SIMSENSE_OK;
+}
+
+const char* simsense_strerror(int code)
+{
+    switch (code) {
+        case SIMSENSE_OK: return "ok";
+        case SIMSENSE_ERR_INVALID_ARG: return "invalid argument";
+        case SIMSENSE_ERR_OOM: return "out of device memory";
+        case SIMSENSE_ERR_CUDA: return "CUDA error";
+        case SIMSENSE_ERR_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int simsense_last_cuda_error(simsense_t h)
+{
+    return h ? h->last_cuda_error : 0;
+}
+
+}  // extern "C"

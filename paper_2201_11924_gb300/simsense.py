@@ -1,0 +1,213 @@
+"""Python binding of libsimsense (C ABI in include/simsense.h).
+
+Argument marshalling only: every step of the depth stage runs in the CUDA
+library.  PyTorch supplies device memory (tensors) and streams; tensors are
+passed to the library as raw pointers.  There is no CPU path: if the shared
+library is missing or fails to load, every entry point raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsimsense.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CUDA = -3
+ERR_TIMEOUT = -4
+OPT_SUBPIXEL = 1
+OPT_PROFILE = 2
+STAGES = ("census", "paths", "select")
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SimsenseError(RuntimeError):
+    def __init__(self, code: int, what: str, cuda_error: int = 0):
+        self.code = code
+        self.cuda_error = cuda_error
+        msg = f"{what}: {strerror(code) if _lib else code}"
+        if code == ERR_CUDA:
+            msg += f" (cudaError {cuda_error})"
+        super().__init__(msg)
+
+
+class DebugT(ctypes.Structure):
+    _fields_ = [("census_left", ctypes.c_void_p), ("census_right", ctypes.c_void_p),
+                ("aggregated", ctypes.c_void_p), ("disparity_int", ctypes.c_void_p),
+                ("disparity", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+
+
+def load():
+    """Load libsimsense.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2201_11924_gb300._build` (there is no CPU fallback)")
+            lib = ctypes.CDLL(LIB_PATH)
+            P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+            lib.simsense_create.argtypes = [ctypes.POINTER(P), I, I, I, I, I, I, I, I, I, F, F]
+            lib.simsense_compute.argtypes = [P, P, P, P, P]
+            lib.simsense_compute_host.argtypes = [P, P, P, P, P]
+            lib.simsense_compute_debug.argtypes = [P, P, P, P, ctypes.POINTER(DebugT), P]
+            lib.simsense_set_option.argtypes = [P, I, I]
+            lib.simsense_scratch_bytes.argtypes = [P]
+            lib.simsense_scratch_bytes.restype = ctypes.c_size_t
+            lib.simsense_destroy.argtypes = [P]
+            lib.simsense_strerror.argtypes = [I]
+            lib.simsense_strerror.restype = ctypes.c_char_p
+            lib.simsense_last_cuda_error.argtypes = [P]
+            lib.simsense_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
+            lib.simsense_profile_read.restype = ctypes.c_int
+            lib.simsense_stage_name.argtypes = [I]
+            lib.simsense_stage_name.restype = ctypes.c_char_p
+            for fn in ("simsense_create", "simsense_compute", "simsense_compute_host",
+                       "simsense_compute_debug", "simsense_set_option", "simsense_destroy",
+                       "simsense_last_cuda_error"):
+                getattr(lib, fn).restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return load().simsense_strerror(code).decode()
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}, "
+                         f"got {t.dtype} {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class SimSense:
+    """One matcher for W x H pairs with disparities 0 .. D-1 (simsense_create)."""
+
+    def __init__(self, W, H, D, win_w, win_h, P1, P2, paths, uniq_ratio, lr_max_diff, f, baseline,
+                 subpixel: bool = True):
+        lib = load()
+        self.W, self.H, self.D = int(W), int(H), int(D)
+        self._h = ctypes.c_void_p()
+        rc = lib.simsense_create(ctypes.byref(self._h), self.W, self.H, self.D,
+                                 int(win_w) | (int(win_h) << 8), int(P1), int(P2), int(paths),
+                                 int(uniq_ratio), int(lr_max_diff), float(f), float(baseline))
+        if rc != OK:
+            self._h = None
+            raise SimsenseError(rc, "simsense_create")
+        if not subpixel:
+            self.set_option(OPT_SUBPIXEL, 0)
+
+    @classmethod
+    def from_workload(cls, wl):
+        return cls(wl.W, wl.H, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq,
+                   wl.lr_max_diff, wl.f, wl.baseline, subpixel=wl.subpixel)
+
+    def _check(self, rc, what):
+        if rc != OK:
+            err = load().simsense_last_cuda_error(self._h) if rc == ERR_CUDA else 0
+            raise SimsenseError(rc, what, err)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("SimSense handle is closed")
+        return self._h
+
+    def set_option(self, opt: int, value: int):
+        self._check(load().simsense_set_option(self.handle, int(opt), int(value)), "simsense_set_option")
+
+    def profile_read(self):
+        """(dict stage -> summed ms, number of calls) recorded since the last read."""
+        ms = (ctypes.c_double * len(STAGES))()
+        n = ctypes.c_int()
+        self._check(load().simsense_profile_read(self.handle, ms, ctypes.byref(n)), "simsense_profile_read")
+        return {STAGES[i]: float(ms[i]) for i in range(len(STAGES))}, int(n.value)
+
+    def scratch_bytes(self) -> int:
+        return int(load().simsense_scratch_bytes(self.handle))
+
+    def compute(self, left, right, depth=None, stream=None):
+        """Depth (float32 H x W CUDA tensor) of one pair of uint8 H x W CUDA tensors."""
+        import torch
+        shape = (self.H, self.W)
+        if depth is None:
+            depth = torch.empty(shape, dtype=torch.float32, device=left.device)
+        rc = load().simsense_compute(self.handle, _dev_ptr(left, torch.uint8, shape, "left"),
+                                     _dev_ptr(right, torch.uint8, shape, "right"),
+                                     _dev_ptr(depth, torch.float32, shape, "depth"), _stream_ptr(stream))
+        self._check(rc, "simsense_compute")
+        return depth
+
+    def compute_host(self, left, right, depth, stream=None):
+        """Same for host buffers (CPU tensors, ideally pinned); depth is filled
+        once the stream is synchronised."""
+        import torch
+        shape = (self.H, self.W)
+        for t, dt, n in ((left, torch.uint8, "left"), (right, torch.uint8, "right"), (depth, torch.float32, "depth")):
+            if t.is_cuda or t.dtype != dt or tuple(t.shape) != shape or not t.is_contiguous():
+                raise ValueError(f"{n} must be a contiguous host {dt} tensor of shape {shape}")
+        rc = load().simsense_compute_host(self.handle, ctypes.c_void_p(left.data_ptr()),
+                                          ctypes.c_void_p(right.data_ptr()),
+                                          ctypes.c_void_p(depth.data_ptr()), _stream_ptr(stream))
+        self._check(rc, "simsense_compute_host")
+        return depth
+
+    def compute_debug(self, left, right, stream=None, aggregated: bool = True):
+        """Depth plus the intermediate results, as a dict of CUDA tensors."""
+        import torch
+        dev = left.device
+        H, W, D = self.H, self.W, self.D
+        out = {
+            "depth": torch.empty((H, W), dtype=torch.float32, device=dev),
+            "census_left": torch.empty((H, W), dtype=torch.int64, device=dev),
+            "census_right": torch.empty((H, W), dtype=torch.int64, device=dev),
+            "disparity_int": torch.empty((H, W), dtype=torch.int16, device=dev),
+            "disparity": torch.empty((H, W), dtype=torch.float32, device=dev),
+            "mask": torch.empty((H, W), dtype=torch.uint8, device=dev),
+        }
+        if aggregated:
+            out["aggregated"] = torch.empty((H, W, D), dtype=torch.int16, device=dev)
+        dbg = DebugT(out["census_left"].data_ptr(), out["census_right"].data_ptr(),
+                     out["aggregated"].data_ptr() if aggregated else None,
+                     out["disparity_int"].data_ptr(), out["disparity"].data_ptr(), out["mask"].data_ptr())
+        shape = (H, W)
+        rc = load().simsense_compute_debug(self.handle, _dev_ptr(left, torch.uint8, shape, "left"),
+                                           _dev_ptr(right, torch.uint8, shape, "right"),
+                                           ctypes.c_void_p(out["depth"].data_ptr()), ctypes.byref(dbg),
+                                           _stream_ptr(stream))
+        self._check(rc, "simsense_compute_debug")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().simsense_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,74 @@
+"""CPU-side checks of the C ABI: the library builds, loads and exports every
+function include/simsense.h declares, and argument validation rejects
+out-of-range parameters before any CUDA call is made."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(simsense_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_11924_gb300 import _build, simsense
+    _build.build()
+    return simsense.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for want in ("simsense_create", "simsense_compute", "simsense_destroy", "simsense_compute_host",
+                 "simsense_compute_debug", "simsense_set_option", "simsense_strerror"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_strerror(lib):
+    from paper_2201_11924_gb300 import simsense
+    assert simsense.strerror(0) == "ok"
+    assert simsense.strerror(-1) == "invalid argument"
+    assert simsense.strerror(-4).startswith("device-side wait")
+
+
+@pytest.mark.parametrize("args", [
+    # W, H, D, win, P1, P2, paths, uniq, lr, f, b
+    (64, 32, 0, 5 | (5 << 8), 7, 86, 4, 0, 1, 300.0, 0.055),       # D < 1
+    (64, 32, 257, 5 | (5 << 8), 7, 86, 4, 0, 1, 300.0, 0.055),     # D > 256
+    (64, 32, 65, 5 | (5 << 8), 7, 86, 4, 0, 1, 300.0, 0.055),      # D > W
+    (64, 32, 16, 4 | (5 << 8), 7, 86, 4, 0, 1, 300.0, 0.055),      # even window
+    (64, 32, 16, 9 | (9 << 8), 7, 86, 4, 0, 1, 300.0, 0.055),      # 80 bits > 64
+    (64, 32, 16, 5 | (5 << 8), 9, 8, 4, 0, 1, 300.0, 0.055),       # P1 > P2
+    (64, 32, 16, 9 | (7 << 8), 7, 200, 4, 0, 1, 300.0, 0.055),     # nbits + P2 > 255
+    (64, 32, 16, 5 | (5 << 8), 7, 86, 6, 0, 1, 300.0, 0.055),      # paths
+    (64, 32, 16, 5 | (5 << 8), 7, 86, 8, 100, 1, 300.0, 0.055),    # uniqueness ratio
+    (64, 32, 16, 5 | (5 << 8), 7, 86, 8, 0, 1, 0.0, 0.055),        # f
+    (64, 32, 16, 5 | (5 << 8), 7, 86, 8, 0, 1, 300.0, -1.0),       # baseline
+    (4, 32, 4, 5 | (5 << 8), 7, 86, 8, 0, 1, 300.0, 0.055),        # W < window
+])
+def test_create_rejects_bad_arguments(lib, args):
+    h = ctypes.c_void_p()
+    assert lib.simsense_create(ctypes.byref(h), *args) == -1
+    assert not h.value
+
+
+def test_null_handles_are_rejected(lib):
+    assert lib.simsense_compute(None, None, None, None, None) == -1
+    assert lib.simsense_set_option(None, 1, 0) == -1
+    assert lib.simsense_destroy(None) == 0

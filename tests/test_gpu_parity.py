@@ -1,0 +1,172 @@
+"""Parity of the CUDA depth stage (through the C ABI) with the CPU oracle.
+
+Bar: census codes, aggregated costs S, integer disparities and validity masks
+bit-exact; fp32 sub-pixel disparity within 1e-4 px and fp32 depth within
+1e-5 relative of the oracle's fp64 values (the fp32 rounding of one division
+and one sum stays far below both).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_11924_gb300 import configs, scenes
+
+pytestmark = pytest.mark.gpu
+
+DISP_TOL = 1e-4
+DEPTH_RTOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_11924_gb300 import _build, simsense
+    _build.build()
+    return simsense
+
+
+def _run(lib, wl, left, right, aggregated=True):
+    import torch
+    dev = torch.device("cuda:0")
+    with lib.SimSense.from_workload(wl) as m:
+        lt = torch.from_numpy(left).to(dev)
+        rt = torch.from_numpy(right).to(dev)
+        out = m.compute_debug(lt, rt, aggregated=aggregated)
+        depth2 = m.compute(lt, rt)
+        torch.cuda.synchronize()
+        res = {k: v.cpu().numpy() for k, v in out.items()}
+        res["depth_plain"] = depth2.cpu().numpy()
+    return res
+
+
+def _oracle(wl, left, right, want_S=True):
+    return oracle.compute(left, right, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq,
+                          wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline, want_codes=True, want_S=want_S)
+
+
+def _compare(g, o, wl, check_S=True):
+    np.testing.assert_array_equal(g["census_left"].view(np.uint64), o["codes_left"])
+    np.testing.assert_array_equal(g["census_right"].view(np.uint64), o["codes_right"])
+    if check_S:
+        np.testing.assert_array_equal(g["aggregated"].view(np.uint16).astype(np.int32), o["S"])
+    np.testing.assert_array_equal(g["disparity_int"].astype(np.int32), o["dstar"])
+    np.testing.assert_array_equal(g["mask"], o["mask"])
+    valid = o["mask"] == 0
+    assert (g["disparity"][~valid] == -1.0).all()
+    np.testing.assert_allclose(g["disparity"][valid], o["disp"][valid], rtol=0, atol=DISP_TOL)
+    assert (g["depth"][~valid] == 0.0).all()
+    np.testing.assert_allclose(g["depth"][valid], o["depth"][valid], rtol=DEPTH_RTOL, atol=0)
+    # the plain call and the debug call run the same kernels
+    np.testing.assert_array_equal(g["depth_plain"], g["depth"])
+
+
+def _small(name, W, H, D, ww, wh, paths, uniq, lr, sub, P1=7, P2=86, seed=1):
+    sc = configs.SMALL_320.scene
+    return configs.Workload(name=name, W=W, H=H, D=D, win_w=ww, win_h=wh, P1=P1, P2=P2, paths=paths,
+                            uniq=uniq, lr_max_diff=lr, subpixel=sub, f=300.0, baseline=0.055, seed=seed,
+                            scene=sc)
+
+
+SMALL_CASES = [
+    # ragged sizes spanning several tiles, every disparity padding class (D
+    # per 32-lane group: 2, 4, 6, 8) and every code width
+    _small("ragged_5x5_4p", 97, 45, 48, 5, 5, 4, 0, 1, False),
+    _small("ragged_7x7_8p_uniq", 150, 70, 96, 7, 7, 8, 15, 1, True, seed=2),
+    _small("ragged_9x7_8p_D160", 300, 33, 160, 9, 7, 8, 10, 1, True, seed=3),
+    _small("ragged_9x7_8p_D256", 260, 40, 256, 9, 7, 8, 10, 0, True, seed=4),
+    _small("D64_exact_4p", 130, 50, 64, 7, 7, 4, 5, 2, True, seed=5),
+    _small("D1", 20, 9, 1, 3, 3, 8, 0, 1, True, seed=6),
+    _small("D_equals_W", 40, 12, 40, 5, 5, 8, 15, 1, True, seed=7),
+    _small("tiny_window_size", 9, 7, 3, 9, 7, 8, 0, 0, True, seed=8),
+    _small("zero_penalties", 80, 30, 32, 5, 5, 8, 0, -1, True, P1=0, P2=0, seed=9),
+    _small("equal_penalties", 80, 30, 32, 7, 7, 4, 99, 3, True, P1=20, P2=20, seed=10),
+    _small("max_P2", 90, 20, 70, 9, 7, 8, 50, 1, True, P1=0, P2=193, seed=11),
+    _small("win_15x3", 70, 25, 40, 15, 3, 8, 0, 1, True, seed=12),
+    _small("win_1x1", 30, 10, 8, 3, 1, 4, 0, 1, True, seed=13),
+]
+
+
+@pytest.mark.parametrize("wl", SMALL_CASES, ids=lambda w: w.name)
+def test_parity_small(lib, wl):
+    p = scenes.make_pair(wl)
+    g = _run(lib, wl, p["left"], p["right"])
+    o = _oracle(wl, p["left"], p["right"])
+    _compare(g, o, wl)
+
+
+def test_parity_small_workload_320(lib):
+    wl = configs.SMALL_320
+    p = scenes.make_pair(wl)
+    _compare(_run(lib, wl, p["left"], p["right"]), _oracle(wl, p["left"], p["right"]), wl)
+
+
+def test_parity_hd_720_full(lib):
+    wl = configs.HD_720
+    p = scenes.make_pair(wl)
+    _compare(_run(lib, wl, p["left"], p["right"]), _oracle(wl, p["left"], p["right"]), wl)
+
+
+def test_parity_fhd_1080_full(lib):
+    wl = configs.FHD_1080
+    p = scenes.make_pair(wl)
+    _compare(_run(lib, wl, p["left"], p["right"]), _oracle(wl, p["left"], p["right"]), wl)
+
+
+def test_plane_exact_recovery_gpu(lib):
+    # noise-free fronto-parallel plane: d* = d0 on every pixel whose census
+    # windows match exactly (the oracle pins the same property)
+    W, H, D, d0 = 200, 60, 64, 17
+    wl = _small("plane", W, H, D, 7, 7, 8, 0, -1, False)
+    p = scenes.make_plane_pair(W, H, d0, seed=3)
+    g = _run(lib, wl, p["left"], p["right"], aggregated=False)
+    xs = np.arange(W)
+    inner = (xs >= d0 + 3) & (xs <= W - 4)
+    assert (g["disparity_int"][:, inner] == d0).all()
+
+
+def test_constant_images(lib):
+    # flat images: all codes 0, every cost 0 -> S constant per pixel -> d* = 0
+    wl = _small("flat", 64, 16, 16, 5, 5, 8, 0, 1, True)
+    left = np.full((16, 64), 90, dtype=np.uint8)
+    g = _run(lib, wl, left, left.copy())
+    o = _oracle(wl, left, left.copy())
+    _compare(g, o, wl)
+    assert (g["disparity_int"] == 0).all() and (g["depth"] == 0).all()
+
+
+def test_host_buffers_match_device_path(lib):
+    import torch
+    wl = configs.SMALL_320
+    p = scenes.make_pair(wl)
+    with lib.SimSense.from_workload(wl) as m:
+        lt = torch.from_numpy(p["left"]).pin_memory()
+        rt = torch.from_numpy(p["right"]).pin_memory()
+        dh = torch.empty((wl.H, wl.W), dtype=torch.float32).pin_memory()
+        m.compute_host(lt, rt, dh)
+        dd = m.compute(lt.cuda(), rt.cuda())
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(dh.numpy(), dd.cpu().numpy())
+
+
+def test_repeat_runs_are_identical(lib):
+    import torch
+    wl = configs.HD_720
+    p = scenes.make_pair(wl)
+    with lib.SimSense.from_workload(wl) as m:
+        lt, rt = torch.from_numpy(p["left"]).cuda(), torch.from_numpy(p["right"]).cuda()
+        a = m.compute(lt, rt).clone()
+        for _ in range(3):
+            b = m.compute(lt, rt)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+
+
+def test_bad_tensor_arguments_raise(lib):
+    import torch
+    with lib.SimSense(64, 32, 16, 5, 5, 7, 86, 4, 0, 1, 300.0, 0.055) as m:
+        good = torch.zeros((32, 64), dtype=torch.uint8, device="cuda")
+        with pytest.raises(ValueError):
+            m.compute(good.float(), good)
+        with pytest.raises(ValueError):
+            m.compute(good[:, :32], good)
+        with pytest.raises(ValueError):
+            m.compute(good.cpu(), good)
