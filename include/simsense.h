@@ -144,6 +144,42 @@ int simsense_compute_debug(simsense_t h, const uint8_t* left_u8, const uint8_t* 
                            float* depth_f32, const simsense_debug_t* dbg,
                            struct CUstream_st* stream);
 
+/*
+ * No-allocation variant of simsense_compute (the paper has no counterpart;
+ * this is a deployment aid).  For callers that may not allocate device memory
+ * at all: a plugin whose host application owns all device memory through its
+ * own pool, a real-time loop that bans allocation after start-up because
+ * cudaMalloc can block the host and synchronise the device, or a process whose
+ * memory is already held by another framework's caching allocator.  Such a
+ * caller cannot use simsense_create, which allocates the handle's scratch.
+ *
+ * This call takes the parameters of simsense_create (same ranges) plus the
+ * sub-pixel switch (0/1) and the device buffers of one pair, and runs the same
+ * kernels as simsense_compute on a fixed scratch array that is part of the
+ * library image (SIMSENSE_NOALLOC_SCRATCH_BYTES on every GPU that loads the
+ * library's code, held until the process exits).  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   - The problem must fit: 2 * round256(W*H*code bytes) + paths*W*H*Dp
+ *     <= SIMSENSE_NOALLOC_SCRATCH_BYTES, with code bytes = 4 when
+ *     w*h - 1 <= 32 else 8, and Dp = 64 * ceil(D/64).  Larger problems, like
+ *     any other out-of-range argument, return SIMSENSE_ERR_INVALID_ARG.
+ *     (320x240, D = 64, 4 paths fits; 1280x720 does not.)
+ *   - The first call on a device looks up the array's device address with that
+ *     device current (a one-time set-up per device); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array: calls whose kernels overlap on the GPU
+ *     (different streams or threads) race; order them, e.g. on one stream.
+ *     Nothing in the array needs clearing between calls, since every byte a
+ *     call reads is written earlier in the same call.
+ * Asynchronous on stream like simsense_compute; SIMSENSE_ERR_CUDA reports a
+ * failed launch (there is no handle to keep the CUDA error code).
+ */
+#define SIMSENSE_NOALLOC_SCRATCH_BYTES (32u << 20)
+int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* right_u8, float* depth_f32,
+                             int W, int H, int D, int census_win, int P1, int P2, int paths,
+                             int uniq_ratio, int lr_max_diff, float f, float baseline,
+                             int subpixel, struct CUstream_st* stream);
+
 /* Set an option (SIMSENSE_OPT_*).  Takes effect at the next compute call. */
 int simsense_set_option(simsense_t h, int opt, int value);
 
