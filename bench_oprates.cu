@@ -1,0 +1,192 @@
+// Per-SM issue rates of the instructions an SGM recurrence can use (GB300 probe).
+// Build and run: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/oprates bench_oprates.cu && /tmp/oprates
+// grid = #SMs blocks x 1024 threads, each thread 8 dependent-rotating chains.
+#include <cstdio>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+
+template <int OP>
+__device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    if constexpr (OP == 0) asm volatile("add.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 1) asm volatile("min.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 2) asm volatile("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 3) asm volatile("xor.b32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 4) asm volatile("prmt.b32 %0, %1, %2, 0x5432;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 5) asm volatile("popc.b32 %0, %1;" : "=r"(d) : "r"(a ^ 0));
+    else if constexpr (OP == 6) asm volatile("shfl.sync.bfly.b32 %0, %1, 1, 0x1f, 0xffffffff;" : "=r"(d) : "r"(a));
+    else if constexpr (OP == 7) asm volatile("mad.lo.u32 %0, %1, %2, 7;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 8) asm volatile("min.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 9) asm volatile("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 10) asm volatile("fma.rn.f16x2 %0, %1, %2, %1;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 11) asm volatile("min.f32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 12) asm volatile("add.rn.f32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 13) d = __vminu4(a, b);
+    else if constexpr (OP == 14) asm volatile("min.bf16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 15) asm volatile("min.f32 %0, %1, %2, %1;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 16) asm volatile("add.u32 %0, %1, %2;\n\tadd.u32 %0, %0, %1;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 17) asm volatile("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 18) asm volatile("vadd2.u32.u32.u32 %0, %1, %2, %1;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 19) asm volatile("sub.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 20) asm volatile("min.u16x2 %0, %1, %2;\n\tmin.f16x2 %0, %0, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 21) asm volatile("redux.sync.min.u32 %0, %1, 0xffffffff;" : "=r"(d) : "r"(a));
+    else if constexpr (OP == 22) asm volatile("min.u16x2 %0, %1, %2;\n\tadd.u32 %0, %0, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 23) asm volatile("min.u16x2 %0, %1, %2;\n\tadd.rn.f16x2 %0, %0, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 24) asm volatile("min.u32 %0, %1, %2;\n\tmin.f32 %0, %0, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 25) asm volatile("min.u16x2 %0, %1, %2;\n\tprmt.b32 %0, %0, %2, 0x5432;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 26) asm volatile("min.f16x2 %0, %1, %2;\n\tadd.rn.f16x2 %0, %0, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 27) asm volatile("min.u16x2 %0, %1, %2;\n\tmad.lo.u32 %0, %0, %2, 7;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
+template <int OP>
+__global__ void __launch_bounds__(1024) kern(uint32_t* out, long long* cyc, int iters, uint32_t seed)
+{
+    uint32_t x[8];
+#pragma unroll
+    for (int i = 0; i < 8; i++) x[i] = seed * (threadIdx.x + i * 7919u) + i;
+    __syncthreads();
+    long long t0 = clock64();
+    for (int it = 0; it < iters; it++) {
+#pragma unroll
+        for (int i = 0; i < 8; i++) x[i] = op<OP>(x[i], x[(i + 1) & 7]);
+    }
+    __syncthreads();
+    long long t1 = clock64();
+    uint32_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 8; i++) acc ^= x[i];
+    out[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+}
+
+template <int OP>
+void run(const char* name, int nsm, uint32_t* out, long long* cyc, int ops_per_asm = 1)
+{
+    const int iters = 4096;
+    kern<OP><<<nsm, 1024>>>(out, cyc, iters, 12345u);
+    kern<OP><<<nsm, 1024>>>(out, cyc, iters, 12345u);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { printf("%s: error %s\n", name, cudaGetErrorString(e)); return; }
+    long long h[1024];
+    cudaMemcpy(h, cyc, nsm * sizeof(long long), cudaMemcpyDeviceToHost);
+    long long mx = 0;
+    for (int i = 0; i < nsm; i++) mx = h[i] > mx ? h[i] : mx;
+    double ops = 1024.0 * iters * 8 * ops_per_asm;
+    printf("%-22s %7.1f results/clk/SM\n", name, ops / (double)mx);
+}
+
+// L2 reduction throughput: every thread adds into its own 16-byte slot of an
+// L2-resident buffer (n_slots slots, grid-stride), `iters` times.
+__global__ void red_v4f16x2(uint4* buf, size_t n_slots, int iters)
+{
+    size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    uint32_t one = 0x3c003c00u;   // (1.0, 1.0) in f16x2
+    for (int it = 0; it < iters; it++)
+        for (size_t i = i0; i < n_slots; i += stride)
+            asm volatile("red.global.add.noftz.v4.f16x2 [%0], {%1, %1, %1, %1};" :: "l"(buf + i), "r"(one) : "memory");
+}
+__global__ void red_u32(uint32_t* buf, size_t n, int iters)
+{
+    size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int it = 0; it < iters; it++)
+        for (size_t i = i0; i < n; i += stride)
+            asm volatile("red.global.add.u32 [%0], 1;" :: "l"(buf + i) : "memory");
+}
+__global__ void st_v4(uint4* buf, size_t n_slots, int iters)
+{
+    size_t i0 = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int it = 0; it < iters; it++)
+        for (size_t i = i0; i < n_slots; i += stride)
+            buf[i] = make_uint4(it, it, it, it);
+}
+
+void mem_probe(int nsm)
+{
+    const size_t bytes = 32u << 20;   // 32 MiB: stays in L2
+    void* buf;
+    if (cudaMalloc(&buf, bytes) != cudaSuccess) { printf("alloc failed\n"); return; }
+    cudaMemset(buf, 0, bytes);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int iters = 20;
+    float ms;
+    size_t slots = bytes / 16;
+    red_v4f16x2<<<nsm * 4, 512>>>((uint4*)buf, slots, 1);
+    cudaEventRecord(e0);
+    red_v4f16x2<<<nsm * 4, 512>>>((uint4*)buf, slots, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("red.v4.f16x2 (32 MiB, L2)  %8.1f GB/s payload, %6.1f G red/s\n", bytes * (double)iters / ms / 1e6,
+           slots * (double)iters / ms / 1e6);
+    red_u32<<<nsm * 4, 512>>>((uint32_t*)buf, bytes / 4, 1);
+    cudaEventRecord(e0);
+    red_u32<<<nsm * 4, 512>>>((uint32_t*)buf, bytes / 4, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("red.u32     (32 MiB, L2)  %8.1f GB/s payload, %6.1f G red/s\n", bytes * (double)iters / ms / 1e6,
+           bytes / 4 * (double)iters / ms / 1e6);
+    st_v4<<<nsm * 4, 512>>>((uint4*)buf, slots, 1);
+    cudaEventRecord(e0);
+    st_v4<<<nsm * 4, 512>>>((uint4*)buf, slots, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    cudaEventElapsedTime(&ms, e0, e1);
+    printf("st.v4       (32 MiB, L2)  %8.1f GB/s\n", bytes * (double)iters / ms / 1e6);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) printf("mem probe error %s\n", cudaGetErrorString(e));
+    cudaFree(buf);
+}
+
+int main()
+{
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0);
+    int clk = 0;
+    cudaDeviceGetAttribute(&clk, cudaDevAttrClockRate, 0);
+    printf("SMs %d, clock attr %d kHz\n", nsm, clk);
+    uint32_t* out;
+    long long* cyc;
+    cudaMalloc(&out, (size_t)nsm * 1024 * 4);
+    cudaMalloc(&cyc, nsm * sizeof(long long));
+    run<0>("add.u32", nsm, out, cyc);
+    run<19>("sub.u32", nsm, out, cyc);
+    run<16>("add.u32 x2 (fusable)", nsm, out, cyc, 2);
+    run<1>("min.u32", nsm, out, cyc);
+    run<2>("min.u16x2", nsm, out, cyc);
+    run<17>("max.u16x2", nsm, out, cyc);
+    run<3>("xor.b32", nsm, out, cyc);
+    run<4>("prmt.b32", nsm, out, cyc);
+    run<5>("popc.b32", nsm, out, cyc);
+    run<6>("shfl.bfly", nsm, out, cyc);
+    run<7>("mad.lo.u32", nsm, out, cyc);
+    run<8>("min.f16x2", nsm, out, cyc);
+    run<9>("add.f16x2", nsm, out, cyc);
+    run<10>("fma.f16x2", nsm, out, cyc);
+    run<14>("min.bf16x2", nsm, out, cyc);
+    run<11>("min.f32", nsm, out, cyc);
+    run<15>("min.f32 3-input", nsm, out, cyc);
+    run<12>("add.f32", nsm, out, cyc);
+    run<13>("__vminu4", nsm, out, cyc);
+    run<18>("vadd2", nsm, out, cyc);
+    run<20>("min.u16x2 + min.f16x2", nsm, out, cyc, 2);
+    run<24>("min.u32 + min.f32", nsm, out, cyc, 2);
+    run<22>("min.u16x2 + add.u32", nsm, out, cyc, 2);
+    run<23>("min.u16x2 + add.f16x2", nsm, out, cyc, 2);
+    run<26>("min.f16x2 + add.f16x2", nsm, out, cyc, 2);
+    run<25>("min.u16x2 + prmt", nsm, out, cyc, 2);
+    run<27>("min.u16x2 + mad.lo.u32", nsm, out, cyc, 2);
+    run<21>("redux.sync.min", nsm, out, cyc);
+    mem_probe(nsm);
+    cudaFree(out);
+    cudaFree(cyc);
+    return 0;
+}

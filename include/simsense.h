@@ -73,9 +73,10 @@ typedef struct simsense_ctx* simsense_t;
 
 /* stages timed under SIMSENSE_OPT_PROFILE, in launch order */
 #define SIMSENSE_STAGE_CENSUS       0     /* census transform of both views */
-#define SIMSENSE_STAGE_PATHS        1     /* matching cost + SGM path aggregation */
-#define SIMSENSE_STAGE_SELECT       2     /* sum of paths, WTA, checks, sub-pixel, depth */
-#define SIMSENSE_NUM_STAGES         3
+#define SIMSENSE_STAGE_COST         1     /* Hamming matching cost volume */
+#define SIMSENSE_STAGE_PATHS        2     /* SGM path aggregation */
+#define SIMSENSE_STAGE_SELECT       3     /* sum of paths, WTA, checks, sub-pixel, depth */
+#define SIMSENSE_NUM_STAGES         4
 
 /* census_win packs the window as w | (h << 8); h = 0 means a square w x w. */
 #define SIMSENSE_WIN(w, h) ((w) | ((h) << 8))
@@ -159,9 +160,9 @@ int simsense_compute_debug(simsense_t h, const uint8_t* left_u8, const uint8_t* 
  * library image (SIMSENSE_NOALLOC_SCRATCH_BYTES on every GPU that loads the
  * library's code, held until the process exits).  It calls no cudaMalloc,
  * cudaFree or allocating library routine.
- *   - The problem must fit: 2 * round256(W*H*code bytes) + paths*W*H*Dp
- *     <= SIMSENSE_NOALLOC_SCRATCH_BYTES, with code bytes = 4 when
- *     w*h - 1 <= 32 else 8, and Dp = 64 * ceil(D/64).  Larger problems, like
+ *   - The problem must fit: 2 * round256(W*H*code bytes)
+ *     + round256(W*H*Dp) + paths*W*H*Dp <= SIMSENSE_NOALLOC_SCRATCH_BYTES,
+ *     with code bytes = 4 when w*h - 1 <= 32 else 8, and Dp = 64 * ceil(D/64).  Larger problems, like
  *     any other out-of-range argument, return SIMSENSE_ERR_INVALID_ARG.
  *     (320x240, D = 64, 4 paths fits; 1280x720 does not.)
  *   - The first call on a device looks up the array's device address with that

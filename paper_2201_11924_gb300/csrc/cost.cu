@@ -1,0 +1,93 @@
+// Hamming matching cost volume (arxiv 2201.11924 Sec. VI-D: "hamming distance
+// as the cost function"; the section computes the cost from shared memory for
+// data reuse).
+//
+// C(x, y, d) = popcount(cL(x, y) ^ cR(x - d, y)) for x - d >= 0, else nbits,
+// stored once per cell as a byte, layout [y][x][Dp] (d fastest).  Every SGM
+// path reads it instead of recomputing it: POPC issues at only 16 results per
+// clock per SM on this GPU, so one evaluation per cell instead of one per path
+// removes the dominant instruction of the aggregation.
+//
+// A block covers 64 pixels of one row; it stages their left codes and the
+// right codes of [x0 - Dp + 1, x0 + 63] in shared memory.  Lane l of a warp
+// handles d = l + 32 j, so the 32 lanes read 32 consecutive right codes
+// (conflict-free) and write 32 consecutive bytes.  Disparities D <= d < Dp
+// that pad the range get cost 255: with every real path cost at most
+// nbits + P2 <= 255, a padded cell never becomes a strict minimum and never
+// undercuts a real neighbour, so it behaves like the +infinity of the
+// recurrence's boundary.
+#include "internal.h"
+
+namespace simsense {
+namespace {
+
+constexpr int kCostPix = 64;
+constexpr int kCostThreads = 256;
+
+__device__ __forceinline__ uint32_t popc(uint32_t v) { return __popc(v); }
+__device__ __forceinline__ uint32_t popc(uint64_t v) { return __popcll(v); }
+
+template <typename CodeT, int DPT>
+__global__ void __launch_bounds__(kCostThreads)
+cost_kernel(const CodeT* __restrict__ cL, const CodeT* __restrict__ cR, int W, int D, int nbits,
+            uint8_t* __restrict__ C)
+{
+    constexpr int Dp = 32 * DPT;
+    __shared__ CodeT sR[kCostPix + Dp];
+    __shared__ CodeT sL[kCostPix];
+    const int y = blockIdx.y, x0 = blockIdx.x * kCostPix;
+    const CodeT* rowL = cL + (size_t)y * W;
+    const CodeT* rowR = cR + (size_t)y * W;
+    for (int i = threadIdx.x; i < kCostPix + Dp - 1; i += kCostThreads) {
+        const int x = x0 - (Dp - 1) + i;
+        sR[i] = (x >= 0 && x < W) ? rowR[x] : (CodeT)0;
+    }
+    for (int i = threadIdx.x; i < kCostPix; i += kCostThreads) {
+        const int x = x0 + i;
+        sL[i] = x < W ? rowL[x] : (CodeT)0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int p = warp; p < kCostPix; p += kCostThreads / 32) {
+        const int x = x0 + p;
+        if (x >= W) break;
+        const CodeT cl = sL[p];
+        uint8_t* out = C + ((size_t)y * W + x) * Dp;
+#pragma unroll
+        for (int j = 0; j < DPT; j++) {
+            const int d = lane + 32 * j;
+            uint32_t c;
+            if (d >= D) c = 255u;
+            else if (x < d) c = (uint32_t)nbits;
+            else c = popc(cl ^ sR[p - d + Dp - 1]);   // sR index of x - d
+            out[d] = (uint8_t)c;
+        }
+    }
+}
+
+template <typename CodeT>
+cudaError_t launch_code(const Params& p, const void* cl, const void* cr, uint8_t* C, cudaStream_t s)
+{
+    dim3 grid((p.W + kCostPix - 1) / kCostPix, p.H);
+    const CodeT* a = (const CodeT*)cl;
+    const CodeT* b = (const CodeT*)cr;
+    switch (p.dpt) {
+        case 2: cost_kernel<CodeT, 2><<<grid, kCostThreads, 0, s>>>(a, b, p.W, p.D, p.nbits, C); break;
+        case 4: cost_kernel<CodeT, 4><<<grid, kCostThreads, 0, s>>>(a, b, p.W, p.D, p.nbits, C); break;
+        case 6: cost_kernel<CodeT, 6><<<grid, kCostThreads, 0, s>>>(a, b, p.W, p.D, p.nbits, C); break;
+        case 8: cost_kernel<CodeT, 8><<<grid, kCostThreads, 0, s>>>(a, b, p.W, p.D, p.nbits, C); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_cost(const Params& p, const void* codes_left, const void* codes_right, uint8_t* C,
+                        cudaStream_t s)
+{
+    if (p.wide_codes) return launch_code<uint64_t>(p, codes_left, codes_right, C, s);
+    return launch_code<uint32_t>(p, codes_left, codes_right, C, s);
+}
+
+}  // namespace simsense

@@ -21,7 +21,7 @@ struct Params {
     int uniq, lr_max_diff;
     int subpixel;
     float f, baseline, fb;   // fb = (float)((double)f * (double)baseline)
-    int dpt;                 // disparities per lane of a 32-lane scanline group
+    int dpt;                 // disparities per lane of a 32-lane scanline group (2, 4, 6, 8)
     int Dp;                  // padded disparity pitch = 32 * dpt
     bool wide_codes;         // census codes need 64 bits (nbits > 32)
 };
@@ -30,7 +30,8 @@ struct Params {
 struct Scratch {
     void* codes_left = nullptr;    // H x W uint32 or uint64
     void* codes_right = nullptr;
-    uint8_t* paths = nullptr;      // paths x H x W x Dp uint8, L_r per path
+    uint8_t* cost = nullptr;       // H x W x Dp uint8, Hamming cost C
+    uint8_t* paths = nullptr;      // H x W x paths x Dp uint8, L_r per path
     uint8_t* stage_left = nullptr; // host-call staging: H x W uint8
     uint8_t* stage_right = nullptr;
     float* stage_depth = nullptr;  // H x W float32
@@ -48,8 +49,9 @@ struct SelectDebug {
 cudaError_t launch_census(const Params& p, const uint8_t* left, const uint8_t* right,
                           void* codes_left, void* codes_right, cudaStream_t s);
 cudaError_t launch_widen_codes(const Params& p, const void* codes, uint64_t* out, cudaStream_t s);
-cudaError_t launch_paths(const Params& p, const void* codes_left, const void* codes_right,
-                         uint8_t* paths, cudaStream_t s);
+cudaError_t launch_cost(const Params& p, const void* codes_left, const void* codes_right,
+                        uint8_t* cost, cudaStream_t s);
+cudaError_t launch_paths(const Params& p, const uint8_t* cost, uint8_t* paths, cudaStream_t s);
 cudaError_t launch_select(const Params& p, const uint8_t* paths, float* depth,
                           const SelectDebug& dbg, cudaStream_t s);
 

@@ -3,88 +3,116 @@
 // consistency check, disparity to depth) fused into one kernel per image row.
 //
 // One block per row.  Each warp takes pixels x of the row in turn, its lanes
-// holding the same disparities as in the path kernel.  Per pixel it
-//   - sums the paths' L_r bytes into S(x, d) (<= 8 * 255, exact in 32 bits);
-//   - finds d* = argmin S with the smallest d on ties by a warp min-reduction
-//     of the key (S << 9) | d;
-//   - runs the uniqueness test against every d with |d - d*| > 1;
-//   - offers every cell to the right view: the right pixel xr = x - d keeps
-//     the minimum key over the cells that map to it (a shared-memory atomicMin),
+// holding the same DPT consecutive disparities as in the path kernel.  A
+// pixel's path costs are contiguous ([y][x][r][Dp]); a lane sums its bytes of
+// every path with two masked 32-bit adds per word (even and odd bytes as
+// packed 16-bit pairs; the sum of 8 bytes cannot carry out of a half).  Then
+//   - d* = argmin S with the smallest d on ties: warp min-reduction of the key
+//     (S << 9) | d;
+//   - the uniqueness test against every d with |d - d*| > 1;
+//   - every cell is offered to the right view: right pixel xr = x - d keeps
+//     the minimum key over the cells mapping to it (shared-memory atomicMin),
 //     which is argmin_d S(xr + d, d) with ties to the smallest d;
-//   - fits the parabola through S(d*-1), S(d*), S(d*+1).
-// After the whole row is in, each pixel's left-right check reads D_R(x - d*)
+//   - the parabola through S(d*-1), S(d*), S(d*+1).
+// When the whole row is in, each pixel's left-right check reads D_R(x - d*)
 // and the depth f*b/d_f is written.
 #include "internal.h"
 
 namespace simsense {
 namespace {
 
-constexpr int kSelThreads = 256;
+constexpr int kSelThreads = 1024;
 constexpr int kSelWarps = kSelThreads / 32;
 
-template <int DPT>
-__device__ __forceinline__ void load_add(const uint8_t* src, uint32_t (&acc)[DPT])
+// The lane's DPT bytes of one path, as words (2*NP bytes).
+template <int NP>
+struct Words { uint32_t w[(NP + 1) / 2]; };
+
+template <int NP>
+__device__ __forceinline__ Words<NP> load_words(const uint8_t* p)
 {
-    if constexpr (DPT == 2) {
-        uint32_t v = *reinterpret_cast<const uint16_t*>(src);
-        acc[0] += v & 0xff; acc[1] += v >> 8;
-    } else if constexpr (DPT == 4) {
-        uint32_t v = *reinterpret_cast<const uint32_t*>(src);
-#pragma unroll
-        for (int j = 0; j < 4; j++) acc[j] += (v >> (8 * j)) & 0xff;
-    } else if constexpr (DPT == 6) {
-        const uint16_t* s16 = reinterpret_cast<const uint16_t*>(src);
-#pragma unroll
-        for (int k = 0; k < 3; k++) {
-            uint32_t v = s16[k];
-            acc[2 * k] += v & 0xff; acc[2 * k + 1] += v >> 8;
-        }
+    Words<NP> r;
+    if constexpr (NP == 1) {
+        r.w[0] = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    } else if constexpr (NP == 2) {
+        r.w[0] = __ldcs(reinterpret_cast<const unsigned int*>(p));
+    } else if constexpr (NP == 3) {
+        const unsigned short* q = reinterpret_cast<const unsigned short*>(p);
+        r.w[0] = (uint32_t)__ldcs(q) | ((uint32_t)__ldcs(q + 1) << 16);
+        r.w[1] = __ldcs(q + 2);
     } else {
-        uint2 v = *reinterpret_cast<const uint2*>(src);
+        uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
+        r.w[0] = v.x;
+        r.w[1] = v.y;
+    }
+    return r;
+}
+
+// Sum of all paths for the lane's cells.  even[k] holds cells (4k, 4k+2),
+// odd[k] cells (4k+1, 4k+3) of the lane's range, as 16-bit pairs.
+template <int NP>
+__device__ __forceinline__ void sum_paths(const uint8_t* src, int paths, int Dp,
+                                          uint32_t (&even)[(NP + 1) / 2], uint32_t (&odd)[(NP + 1) / 2])
+{
+    constexpr int NW = (NP + 1) / 2;
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            acc[j] += (v.x >> (8 * j)) & 0xff;
-            acc[4 + j] += (v.y >> (8 * j)) & 0xff;
+    for (int k = 0; k < NW; k++) { even[k] = 0; odd[k] = 0; }
+    Words<NP> buf[8];
+#pragma unroll
+    for (int r = 0; r < 8; r++)
+        if (r < paths) buf[r] = load_words<NP>(src + r * Dp);
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        if (r < paths) {
+#pragma unroll
+            for (int k = 0; k < NW; k++) {
+                even[k] += buf[r].w[k] & 0x00ff00ffu;
+                odd[k] += (buf[r].w[k] >> 8) & 0x00ff00ffu;
+            }
         }
     }
 }
 
-template <int DPT>
+template <int NP>
 __global__ void __launch_bounds__(kSelThreads)
-sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int D, int Dp,
-                  int uniq, int lr_max_diff, int subpixel, float fb, float* __restrict__ depth,
-                  SelectDebug dbg)
+sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int uniq, int lr_max_diff,
+                  int subpixel, float fb, float* __restrict__ depth, SelectDebug dbg)
 {
+    constexpr int DPT = 2 * NP;
+    constexpr int Dp = 32 * DPT;
+    constexpr int NW = (NP + 1) / 2;
     extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t* keyR = reinterpret_cast<uint32_t*>(smem);          // W
-    float* dispf = reinterpret_cast<float*>(keyR + W);           // W
-    uint16_t* sbuf = reinterpret_cast<uint16_t*>(dispf + W);     // kSelWarps x Dp
+    uint32_t* keyR = reinterpret_cast<uint32_t*>(smem);              // W
+    float* dispf = reinterpret_cast<float*>(keyR + W);               // W
+    uint16_t* sbuf = reinterpret_cast<uint16_t*>(dispf + W);         // kSelWarps x Dp
     int16_t* dstar = reinterpret_cast<int16_t*>(sbuf + kSelWarps * Dp);  // W
-    uint8_t* ufail = reinterpret_cast<uint8_t*>(dstar + W);      // W
+    uint8_t* ufail = reinterpret_cast<uint8_t*>(dstar + W);          // W
 
     const int y = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < W; i += kSelThreads) keyR[i] = 0xffffffffu;
     __syncthreads();
 
-    const size_t slice = (size_t)H * W * Dp;
     const int d0 = lane * DPT;
+    const size_t pstride = (size_t)paths * Dp;
     uint16_t* sw = sbuf + warp * Dp;
+    const uint8_t* row = vol + (size_t)y * W * pstride + d0;
     for (int x = warp; x < W; x += kSelWarps) {
         const size_t pix = (size_t)y * W + x;
+        uint32_t even[NW], odd[NW];
+        sum_paths<NP>(row + (size_t)x * pstride, paths, Dp, even, odd);
+        // cell j of the lane (d = d0 + j): word j/4, byte j%4
         uint32_t S[DPT];
 #pragma unroll
-        for (int j = 0; j < DPT; j++) S[j] = 0;
-        const uint8_t* src = vol + pix * Dp + d0;
-        for (int r = 0; r < paths; r++) load_add<DPT>(src + r * slice, S);
-
-        uint32_t key[DPT];
+        for (int j = 0; j < DPT; j++) {
+            const uint32_t w = (j & 1) ? odd[j >> 2] : even[j >> 2];
+            S[j] = (j & 2) ? (w >> 16) : (w & 0xffffu);
+        }
         uint32_t kmin = 0xffffffffu;
 #pragma unroll
         for (int j = 0; j < DPT; j++) {
             const int d = d0 + j;
-            key[j] = d < D ? (S[j] << 9) | (uint32_t)d : 0xffffffffu;
-            kmin = min(kmin, key[j]);
+            if (d < D) kmin = min(kmin, (S[j] << 9) | (uint32_t)d);
         }
         kmin = __reduce_min_sync(0xffffffffu, kmin);
         const int ds = (int)(kmin & 511u);
@@ -92,11 +120,13 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int 
 
         bool bad = false;
         if (uniq > 0) {
+            const uint32_t lim = 100u * smin;
+            const uint32_t u = (uint32_t)(100 - uniq);
 #pragma unroll
             for (int j = 0; j < DPT; j++) {
                 const int d = d0 + j;
                 const int diff = d > ds ? d - ds : ds - d;
-                if (d < D && diff > 1 && (uint32_t)(100 - uniq) * S[j] < 100u * smin) bad = true;
+                if (d < D && diff > 1 && u * S[j] < lim) bad = true;
             }
         }
         bad = __any_sync(0xffffffffu, bad);
@@ -106,7 +136,7 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int 
             const int d = d0 + j;
             if (d < D) {
                 sw[d] = (uint16_t)S[j];
-                if (d <= x) atomicMin(&keyR[x - d], key[j]);
+                if (d <= x) atomicMin(&keyR[x - d], (S[j] << 9) | (uint32_t)d);
                 if (dbg.aggregated) dbg.aggregated[pix * D + d] = (uint16_t)S[j];
             }
         }
@@ -115,9 +145,7 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int 
             float df = (float)ds;
             if (subpixel && ds >= 1 && ds <= D - 2) {
                 const int sm = sw[ds - 1], sp = sw[ds + 1], s0 = (int)smin;
-                const int num = sm - sp;
-                const int den = 2 * (sm + sp - 2 * s0);
-                df = (float)ds + __fdiv_rn((float)num, (float)den);
+                df = (float)ds + __fdiv_rn((float)(sm - sp), (float)(2 * (sm + sp - 2 * s0)));
             }
             dispf[x] = df;
             dstar[x] = (int16_t)ds;
@@ -150,18 +178,18 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int 
     }
 }
 
-template <int DPT>
+template <int NP>
 cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const SelectDebug& dbg,
                      cudaStream_t s)
 {
     const size_t smem = (size_t)p.W * (4 + 4 + 2 + 1) + (size_t)kSelWarps * p.Dp * 2 + 16;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sgm_select_kernel<DPT>,
+        cudaError_t e = cudaFuncSetAttribute(sgm_select_kernel<NP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sgm_select_kernel<DPT><<<p.H, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.H, p.D, p.Dp, p.uniq,
-                                                          p.lr_max_diff, p.subpixel, p.fb, depth, dbg);
+    sgm_select_kernel<NP><<<p.H, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.D, p.uniq, p.lr_max_diff,
+                                                          p.subpixel, p.fb, depth, dbg);
     return cudaGetLastError();
 }
 
@@ -171,10 +199,10 @@ cudaError_t launch_select(const Params& p, const uint8_t* paths, float* depth, c
                           cudaStream_t s)
 {
     switch (p.dpt) {
-        case 2: return launch_t<2>(p, paths, depth, dbg, s);
-        case 4: return launch_t<4>(p, paths, depth, dbg, s);
-        case 6: return launch_t<6>(p, paths, depth, dbg, s);
-        case 8: return launch_t<8>(p, paths, depth, dbg, s);
+        case 2: return launch_t<1>(p, paths, depth, dbg, s);
+        case 4: return launch_t<2>(p, paths, depth, dbg, s);
+        case 6: return launch_t<3>(p, paths, depth, dbg, s);
+        case 8: return launch_t<4>(p, paths, depth, dbg, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1,5 +1,5 @@
 // C ABI of libsimsense (declared in include/simsense.h): argument checks,
-// scratch ownership and the launch sequence census -> paths -> select.
+// scratch ownership and the launch sequence census -> cost -> paths -> select.
 #include <math.h>
 #include <new>
 
@@ -35,6 +35,7 @@ void free_scratch(Scratch& s)
 {
     cudaFree(s.codes_left);
     cudaFree(s.codes_right);
+    cudaFree(s.cost);
     cudaFree(s.paths);
     cudaFree(s.stage_left);
     cudaFree(s.stage_right);
@@ -69,8 +70,12 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
     if (e == cudaSuccess) e = launch_census(p, left, right, s.codes_left, s.codes_right, st);
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_CENSUS, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
+    e = mark(h, SIMSENSE_STAGE_COST, false, st);
+    if (e == cudaSuccess) e = launch_cost(p, s.codes_left, s.codes_right, s.cost, st);
+    if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_COST, true, st);
+    if (e != cudaSuccess) return cuda_fail(h, e);
     e = mark(h, SIMSENSE_STAGE_PATHS, false, st);
-    if (e == cudaSuccess) e = launch_paths(p, s.codes_left, s.codes_right, s.paths, st);
+    if (e == cudaSuccess) e = launch_paths(p, s.cost, s.paths, st);
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_PATHS, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     SelectDebug sd{};
@@ -138,10 +143,12 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
 
     const size_t npx = (size_t)W * H;
     const size_t code_bytes = npx * (p.wide_codes ? 8 : 4);
+    const size_t cost_bytes = npx * p.Dp;
     const size_t vol_bytes = (size_t)paths * npx * p.Dp;
     Scratch& s = h->s;
     bool ok = cudaMalloc(&s.codes_left, code_bytes) == cudaSuccess &&
               cudaMalloc(&s.codes_right, code_bytes) == cudaSuccess &&
+              cudaMalloc((void**)&s.cost, cost_bytes) == cudaSuccess &&
               cudaMalloc((void**)&s.paths, vol_bytes) == cudaSuccess &&
               cudaMalloc((void**)&s.stage_left, npx) == cudaSuccess &&
               cudaMalloc((void**)&s.stage_right, npx) == cudaSuccess &&
@@ -152,7 +159,7 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
         delete h;
         return SIMSENSE_ERR_OOM;
     }
-    s.bytes = 2 * code_bytes + vol_bytes + 2 * npx + npx * sizeof(float);
+    s.bytes = 2 * code_bytes + cost_bytes + vol_bytes + 2 * npx + npx * sizeof(float);
     *out = h;
     return SIMSENSE_OK;
 }
@@ -248,6 +255,7 @@ const char* simsense_stage_name(int i)
 {
     switch (i) {
         case SIMSENSE_STAGE_CENSUS: return "census";
+        case SIMSENSE_STAGE_COST: return "cost";
         case SIMSENSE_STAGE_PATHS: return "paths";
         case SIMSENSE_STAGE_SELECT: return "select";
         default: return nullptr;

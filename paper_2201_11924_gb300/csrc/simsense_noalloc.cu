@@ -8,8 +8,8 @@
 // streams), or a process whose device memory is already reserved by another
 // framework's caching allocator.  simsense_create allocates the handle's
 // scratch with cudaMalloc, so such callers cannot use it.  This entry point
-// instead takes every parameter per call and runs the same census, path and
-// selection kernels on a scratch buffer that is a file-scope __device__ array
+// instead takes every parameter per call and runs the same census, cost, path
+// and selection kernels on a scratch buffer that is a file-scope __device__ array
 // of fixed size, part of the library image itself.
 //
 // Costs and rules of that choice:
@@ -108,22 +108,26 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
                          subpixel);
     if (rc != SIMSENSE_OK) return rc;
 
-    // carve the fixed array: left codes | right codes | path volume
+    // carve the fixed array: left codes | right codes | cost volume | path volume
     const size_t npx = (size_t)W * H;
     const size_t code_bytes = round256(npx * (p.wide_codes ? 8 : 4));
+    const size_t cost_bytes = round256(npx * p.Dp);
     const size_t vol_bytes = (size_t)paths * npx * p.Dp;
-    if (2 * code_bytes + vol_bytes > (size_t)SIMSENSE_NOALLOC_SCRATCH_BYTES) return SIMSENSE_ERR_INVALID_ARG;
+    if (2 * code_bytes + cost_bytes + vol_bytes > (size_t)SIMSENSE_NOALLOC_SCRATCH_BYTES)
+        return SIMSENSE_ERR_INVALID_ARG;
     void* base = nullptr;
     rc = scratch_address(&base);
     if (rc != SIMSENSE_OK) return rc;
     uint8_t* b = static_cast<uint8_t*>(base);
     void* codes_left = b;
     void* codes_right = b + code_bytes;
-    uint8_t* vol = b + 2 * code_bytes;
+    uint8_t* cost = b + 2 * code_bytes;
+    uint8_t* vol = cost + cost_bytes;
 
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = launch_census(p, left_u8, right_u8, codes_left, codes_right, st);
-    if (e == cudaSuccess) e = launch_paths(p, codes_left, codes_right, vol, st);
+    if (e == cudaSuccess) e = launch_cost(p, codes_left, codes_right, cost, st);
+    if (e == cudaSuccess) e = launch_paths(p, cost, vol, st);
     SelectDebug none{};
     if (e == cudaSuccess) e = launch_select(p, vol, depth_f32, none, st);
     return e == cudaSuccess ? SIMSENSE_OK : SIMSENSE_ERR_CUDA;

@@ -21,7 +21,7 @@ ERR_CUDA = -3
 ERR_TIMEOUT = -4
 OPT_SUBPIXEL = 1
 OPT_PROFILE = 2
-STAGES = ("census", "paths", "select")
+STAGES = ("census", "cost", "paths", "select")
 
 _lock = threading.Lock()
 _lib = None
