@@ -52,15 +52,21 @@ cost_kernel(const CodeT* __restrict__ cL, const CodeT* __restrict__ cR, int W, i
         const int x = x0 + p;
         if (x >= W) break;
         const CodeT cl = sL[p];
-        uint8_t* out = C + ((size_t)y * W + x) * Dp;
+        uint8_t* out = C + ((size_t)y * W + x) * Dp + lane;
+        const CodeT* sr = sR + p + Dp - 1 - lane;        // sr[-32 j] is cR(x - d), d = lane + 32 j
+        if (x >= Dp - 1 && D == Dp) {                    // uniform: every cell is a real match
 #pragma unroll
-        for (int j = 0; j < DPT; j++) {
-            const int d = lane + 32 * j;
-            uint32_t c;
-            if (d >= D) c = 255u;
-            else if (x < d) c = (uint32_t)nbits;
-            else c = popc(cl ^ sR[p - d + Dp - 1]);   // sR index of x - d
-            out[d] = (uint8_t)c;
+            for (int j = 0; j < DPT; j++) out[32 * j] = (uint8_t)popc(cl ^ sr[-32 * j]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < DPT; j++) {
+                const int d = lane + 32 * j;
+                uint32_t c;
+                if (d >= D) c = 255u;
+                else if (x < d) c = (uint32_t)nbits;
+                else c = popc(cl ^ sr[-32 * j]);
+                out[32 * j] = (uint8_t)c;
+            }
         }
     }
 }

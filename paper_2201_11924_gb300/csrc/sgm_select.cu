@@ -2,8 +2,9 @@
 // candidates, uniqueness test, quadratic sub-pixel fitting, left-right
 // consistency check, disparity to depth) fused into one kernel per image row.
 //
-// One block per row.  Each warp takes pixels x of the row in turn, its lanes
-// holding the same DPT consecutive disparities as in the path kernel.  A
+// One block per row.  A group of G lanes takes one pixel (a warp takes 32 / G
+// pixels side by side), each lane holding the same DPT consecutive
+// disparities as in the path kernel.  A
 // pixel's path costs are contiguous ([y][x][r][Dp]); a lane sums its bytes of
 // every path with two masked 32-bit adds per word (even and odd bytes as
 // packed 16-bit pairs; the sum of 8 bytes cannot carry out of a half).  Then
@@ -73,34 +74,39 @@ __device__ __forceinline__ void sum_paths(const uint8_t* src, int paths, int Dp,
     }
 }
 
-template <int NP>
+template <int NP, int G>
 __global__ void __launch_bounds__(kSelThreads)
 sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int uniq, int lr_max_diff,
                   int subpixel, float fb, float* __restrict__ depth, SelectDebug dbg)
 {
     constexpr int DPT = 2 * NP;
-    constexpr int Dp = 32 * DPT;
+    constexpr int Dp = G * DPT;
+    constexpr int SPW = 32 / G;               // pixels a warp takes at once
     constexpr int NW = (NP + 1) / 2;
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* keyR = reinterpret_cast<uint32_t*>(smem);              // W
     float* dispf = reinterpret_cast<float*>(keyR + W);               // W
-    uint16_t* sbuf = reinterpret_cast<uint16_t*>(dispf + W);         // kSelWarps x Dp
-    int16_t* dstar = reinterpret_cast<int16_t*>(sbuf + kSelWarps * Dp);  // W
+    uint16_t* sbuf = reinterpret_cast<uint16_t*>(dispf + W);         // kSelWarps * SPW x Dp
+    int16_t* dstar = reinterpret_cast<int16_t*>(sbuf + kSelWarps * SPW * Dp);  // W
     uint8_t* ufail = reinterpret_cast<uint8_t*>(dstar + W);          // W
 
     const int y = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gl = lane % G, sub = lane / G;
+    const unsigned gmask = SPW > 1 ? (((1u << G) - 1u) << (sub * G)) : 0xffffffffu;
     for (int i = threadIdx.x; i < W; i += kSelThreads) keyR[i] = 0xffffffffu;
     __syncthreads();
 
-    const int d0 = lane * DPT;
+    const int d0 = gl * DPT;
     const size_t pstride = (size_t)paths * Dp;
-    uint16_t* sw = sbuf + warp * Dp;
+    uint16_t* sw = sbuf + (warp * SPW + sub) * Dp;
     const uint8_t* row = vol + (size_t)y * W * pstride + d0;
-    for (int x = warp; x < W; x += kSelWarps) {
+    for (int xb = warp * SPW; xb < W; xb += kSelWarps * SPW) {     // uniform per warp
+        const int x = xb + sub;
+        const bool act = x < W;
         const size_t pix = (size_t)y * W + x;
         uint32_t even[NW], odd[NW];
-        sum_paths<NP>(row + (size_t)x * pstride, paths, Dp, even, odd);
+        sum_paths<NP>(row + (size_t)(act ? x : 0) * pstride, paths, Dp, even, odd);
         // cell j of the lane (d = d0 + j): word j/4, byte j%4
         uint32_t S[DPT];
 #pragma unroll
@@ -114,7 +120,7 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int 
             const int d = d0 + j;
             if (d < D) kmin = min(kmin, (S[j] << 9) | (uint32_t)d);
         }
-        kmin = __reduce_min_sync(0xffffffffu, kmin);
+        kmin = __reduce_min_sync(gmask, kmin);
         const int ds = (int)(kmin & 511u);
         const uint32_t smin = kmin >> 9;
 
@@ -129,19 +135,21 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int 
                 if (d < D && diff > 1 && u * S[j] < lim) bad = true;
             }
         }
-        bad = __any_sync(0xffffffffu, bad);
+        bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
 
+        if (act) {
 #pragma unroll
-        for (int j = 0; j < DPT; j++) {
-            const int d = d0 + j;
-            if (d < D) {
-                sw[d] = (uint16_t)S[j];
-                if (d <= x) atomicMin(&keyR[x - d], (S[j] << 9) | (uint32_t)d);
-                if (dbg.aggregated) dbg.aggregated[pix * D + d] = (uint16_t)S[j];
+            for (int j = 0; j < DPT; j++) {
+                const int d = d0 + j;
+                if (d < D) {
+                    sw[d] = (uint16_t)S[j];
+                    if (d <= x) atomicMin(&keyR[x - d], (S[j] << 9) | (uint32_t)d);
+                    if (dbg.aggregated) dbg.aggregated[pix * D + d] = (uint16_t)S[j];
+                }
             }
         }
         __syncwarp();
-        if (lane == 0) {
+        if (gl == 0 && act) {
             float df = (float)ds;
             if (subpixel && ds >= 1 && ds <= D - 2) {
                 const int sm = sw[ds - 1], sp = sw[ds + 1], s0 = (int)smin;
@@ -178,18 +186,19 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int 
     }
 }
 
-template <int NP>
+template <int NP, int G>
 cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const SelectDebug& dbg,
                      cudaStream_t s)
 {
-    const size_t smem = (size_t)p.W * (4 + 4 + 2 + 1) + (size_t)kSelWarps * p.Dp * 2 + 16;
+    // keyR + dispf + dstar + ufail per pixel of the row, one S row per pixel group
+    const size_t smem = (size_t)p.W * (4 + 4 + 2 + 1) + (size_t)kSelWarps * (32 / G) * p.Dp * 2 + 16;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sgm_select_kernel<NP>,
+        cudaError_t e = cudaFuncSetAttribute(sgm_select_kernel<NP, G>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sgm_select_kernel<NP><<<p.H, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.D, p.uniq, p.lr_max_diff,
-                                                          p.subpixel, p.fb, depth, dbg);
+    sgm_select_kernel<NP, G><<<p.H, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.D, p.uniq, p.lr_max_diff,
+                                                             p.subpixel, p.fb, depth, dbg);
     return cudaGetLastError();
 }
 
@@ -198,11 +207,11 @@ cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const Se
 cudaError_t launch_select(const Params& p, const uint8_t* paths, float* depth, const SelectDebug& dbg,
                           cudaStream_t s)
 {
-    switch (p.dpt) {
-        case 2: return launch_t<1>(p, paths, depth, dbg, s);
-        case 4: return launch_t<2>(p, paths, depth, dbg, s);
-        case 6: return launch_t<3>(p, paths, depth, dbg, s);
-        case 8: return launch_t<4>(p, paths, depth, dbg, s);
+    switch (p.Dp) {                            // the path kernel's lane groups
+        case 64: return launch_t<4, 8>(p, paths, depth, dbg, s);
+        case 128: return launch_t<4, 16>(p, paths, depth, dbg, s);
+        case 192: return launch_t<3, 32>(p, paths, depth, dbg, s);
+        case 256: return launch_t<4, 32>(p, paths, depth, dbg, s);
         default: return cudaErrorInvalidValue;
     }
 }
