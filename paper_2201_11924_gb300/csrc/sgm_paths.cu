@@ -8,8 +8,8 @@
 // 32 / G scanlines side by side); lane l of a group holds the disparities
 // l*DPT .. l*DPT + DPT - 1 of the padded range Dp as DPT/2 packed 16-bit
 // pairs.  At each pixel p the group
-//   1. takes C(p, .) from the byte cost volume (loaded one step ahead, so the
-//      load latency overlaps the previous step);
+//   1. takes C(p, .) from the byte cost volume (loaded 8 steps ahead, so the
+//      load latency overlaps the recurrence);
 //   2. evaluates  L(p,d) = C(p,d) + min(L'(d), L'(d-1)+P1, L'(d+1)+P1, m'+P2) - m'
 //      on the pairs: min(L'(d-1), L'(d+1)) of both cells of a pair is one
 //      min.u16x2 of the pair shifted down and up by one cell (byte permutes
@@ -154,7 +154,10 @@ __device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NP], unsigned 
 }
 
 // G lanes walk one scanline (32 / G scanlines per warp), each holding NP pairs.
-template <int NP, int G>
+// The cost of the next PF pixels is kept in flight in a register ring (slot
+// i % PF, a static index inside the PF-times unrolled loop), which hides the
+// DRAM latency behind PF steps of the recurrence.
+template <int NP, int G, int PF>
 __global__ void __launch_bounds__(kPathThreads)
 sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, int paths,
                  uint8_t* __restrict__ vol)
@@ -178,56 +181,65 @@ sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, in
     const uint32_t p2 = (uint32_t)P2 * 0x10001u;
     const long long pix0 = (long long)y * W + x;
     const long long step = (long long)ry * W + rx;      // pixel index increment along the path
-    const uint8_t* cp = C + pix0 * Dp + gl * DPT;
     const long long cstep = step * Dp;
-    uint8_t* op = vol + (pix0 * paths + r) * Dp + gl * DPT;
     const long long ostep = step * paths * Dp;
+    const uint8_t* cf = C + pix0 * Dp + gl * DPT;        // cost of the next pixel to fetch
+    uint8_t* op = vol + (pix0 * paths + r) * Dp + gl * DPT;
     const uint64_t pol = keep_policy();
 
-    // the entry pixel: L = C
-    Raw<NP> raw{};
-    if (len > 0) raw = load_raw<NP>(cp, pol);
+    Raw<NP> ring[PF] = {};
+#pragma unroll
+    for (int k = 0; k < PF; k++) {
+        if (k < len) ring[k] = load_raw<NP>(cf, pol);
+        cf += cstep;
+    }
+    // L' = 0 and m' = 0 before the entry pixel make the recurrence return
+    // exactly C there, which is the path's start condition.
     uint32_t Lp[NP];
-    unpack<NP>(raw, Lp);
-    if (len > 1) raw = load_raw<NP>(cp + cstep, pol);
-    if (len > 0) store_pairs<NP>(op, Lp);
-    uint32_t mm = group_min<NP>(Lp, gmask);
-    uint32_t cap = mm + p2;
+#pragma unroll
+    for (int k = 0; k < NP; k++) Lp[k] = 0;
+    uint32_t mm = 0, cap = p2;
 
-    for (int i = 1; i < n; i++) {
-        cp += cstep;
-        op += ostep;
-        uint32_t Cp[NP];
-        unpack<NP>(raw, Cp);
-        if (i + 1 < len) raw = load_raw<NP>(cp + cstep, pol);   // one step ahead
-        uint32_t lo = __shfl_up_sync(0xffffffffu, Lp[NP - 1], 1, G);
-        uint32_t hi = __shfl_down_sync(0xffffffffu, Lp[0], 1, G);
-        if (gl == 0) lo = kInfPair;
-        if (gl == G - 1) hi = kInfPair;
-        uint32_t S[NP + 1];
-        S[0] = shift_pair(lo, Lp[0]);
+    for (int base = 0; base < n; base += PF) {
 #pragma unroll
-        for (int k = 1; k < NP; k++) S[k] = shift_pair(Lp[k - 1], Lp[k]);
-        S[NP] = shift_pair(Lp[NP - 1], hi);
+        for (int k = 0; k < PF; k++) {
+            const int i = base + k;
+            if (i >= n) break;                 // uniform
+            uint32_t Cp[NP];
+            unpack<NP>(ring[k], Cp);
+            if (i + PF < len) ring[k] = load_raw<NP>(cf, pol);
+            cf += cstep;
+            uint32_t lo = __shfl_up_sync(0xffffffffu, Lp[NP - 1], 1, G);
+            uint32_t hi = __shfl_down_sync(0xffffffffu, Lp[0], 1, G);
+            if (gl == 0) lo = kInfPair;
+            if (gl == G - 1) hi = kInfPair;
+            uint32_t S[NP + 1];
+            S[0] = shift_pair(lo, Lp[0]);
 #pragma unroll
-        for (int k = 0; k < NP; k++) {
-            uint32_t t = vmin2(S[k], S[k + 1]) + p1;
-            t = vmin2(vmin2(t, Lp[k]), cap);
-            Lp[k] = t + Cp[k] - mm;      // no borrow: every half of t is >= m'
+            for (int q = 1; q < NP; q++) S[q] = shift_pair(Lp[q - 1], Lp[q]);
+            S[NP] = shift_pair(Lp[NP - 1], hi);
+#pragma unroll
+            for (int q = 0; q < NP; q++) {
+                uint32_t t = vmin2(S[q], S[q + 1]) + p1;
+                t = vmin2(vmin2(t, Lp[q]), cap);
+                Lp[q] = t + Cp[q] - mm;      // no borrow: every half of t is >= m'
+            }
+            if (i < len) store_pairs<NP>(op, Lp);
+            op += ostep;
+            mm = group_min<NP>(Lp, gmask);
+            cap = mm + p2;
         }
-        if (i < len) store_pairs<NP>(op, Lp);
-        mm = group_min<NP>(Lp, gmask);
-        cap = mm + p2;
     }
 }
 
 template <int NP, int G>
 cudaError_t launch_t(const Params& p, const uint8_t* C, uint8_t* vol, cudaStream_t s)
 {
+    constexpr int PF = 8;
     const int nscan = p.W + p.H - 1;          // the most scanlines any direction has
     const int per_block = (kPathThreads / 32) * (32 / G);
     dim3 grid((nscan + per_block - 1) / per_block, p.paths);
-    sgm_paths_kernel<NP, G><<<grid, kPathThreads, 0, s>>>(C, p.W, p.H, p.P1, p.P2, p.paths, vol);
+    sgm_paths_kernel<NP, G, PF><<<grid, kPathThreads, 0, s>>>(C, p.W, p.H, p.P1, p.P2, p.paths, vol);
     return cudaGetLastError();
 }
 

@@ -76,8 +76,8 @@ __device__ __forceinline__ void sum_paths(const uint8_t* src, int paths, int Dp,
 
 template <int NP, int G>
 __global__ void __launch_bounds__(kSelThreads)
-sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int uniq, int lr_max_diff,
-                  int subpixel, float fb, float* __restrict__ depth, SelectDebug dbg)
+sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int uniq, uint32_t umagic,
+                  int lr_max_diff, int subpixel, float fb, float* __restrict__ depth, SelectDebug dbg)
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
@@ -114,38 +114,58 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int 
             const uint32_t w = (j & 1) ? odd[j >> 2] : even[j >> 2];
             S[j] = (j & 2) ? (w >> 16) : (w & 0xffffu);
         }
+        // every cell of the group is real and matches inside the image
+        const bool interior = D == Dp && x >= Dp - 1;   // uniform per group
         uint32_t kmin = 0xffffffffu;
+        if (interior) {
 #pragma unroll
-        for (int j = 0; j < DPT; j++) {
-            const int d = d0 + j;
-            if (d < D) kmin = min(kmin, (S[j] << 9) | (uint32_t)d);
+            for (int j = 0; j < DPT; j++) kmin = min(kmin, (S[j] << 9) | (uint32_t)(d0 + j));
+        } else {
+#pragma unroll
+            for (int j = 0; j < DPT; j++) {
+                const int d = d0 + j;
+                if (d < D) kmin = min(kmin, (S[j] << 9) | (uint32_t)d);
+            }
         }
         kmin = __reduce_min_sync(gmask, kmin);
         const int ds = (int)(kmin & 511u);
         const uint32_t smin = kmin >> 9;
 
+        // uniqueness: (100 - u) S(d) < 100 S(d*)  <=>  S(d) < T = ceil(100 S(d*) / (100 - u)),
+        // the division done as a multiply-high by umagic = floor(2^32 / (100 - u)) + 1,
+        // exact for numerators below 2^18
         bool bad = false;
         if (uniq > 0) {
-            const uint32_t lim = 100u * smin;
-            const uint32_t u = (uint32_t)(100 - uniq);
+            const uint32_t T = __umulhi(100u * smin + (uint32_t)(99 - uniq), umagic);
 #pragma unroll
             for (int j = 0; j < DPT; j++) {
                 const int d = d0 + j;
-                const int diff = d > ds ? d - ds : ds - d;
-                if (d < D && diff > 1 && u * S[j] < lim) bad = true;
+                if ((uint32_t)(d - ds + 1) > 2u && d < D && S[j] < T) bad = true;
             }
         }
         bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
 
         if (act) {
+            if (interior) {
 #pragma unroll
-            for (int j = 0; j < DPT; j++) {
-                const int d = d0 + j;
-                if (d < D) {
-                    sw[d] = (uint16_t)S[j];
-                    if (d <= x) atomicMin(&keyR[x - d], (S[j] << 9) | (uint32_t)d);
-                    if (dbg.aggregated) dbg.aggregated[pix * D + d] = (uint16_t)S[j];
+                for (int j = 0; j < DPT; j++) {
+                    sw[d0 + j] = (uint16_t)S[j];
+                    atomicMin(&keyR[x - d0 - j], (S[j] << 9) | (uint32_t)(d0 + j));
                 }
+            } else {
+#pragma unroll
+                for (int j = 0; j < DPT; j++) {
+                    const int d = d0 + j;
+                    if (d < D) {
+                        sw[d] = (uint16_t)S[j];
+                        if (d <= x) atomicMin(&keyR[x - d], (S[j] << 9) | (uint32_t)d);
+                    }
+                }
+            }
+            if (dbg.aggregated) {
+#pragma unroll
+                for (int j = 0; j < DPT; j++)
+                    if (d0 + j < D) dbg.aggregated[pix * D + d0 + j] = (uint16_t)S[j];
             }
         }
         __syncwarp();
@@ -197,8 +217,9 @@ cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const Se
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sgm_select_kernel<NP, G><<<p.H, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.D, p.uniq, p.lr_max_diff,
-                                                             p.subpixel, p.fb, depth, dbg);
+    const uint32_t umagic = p.uniq > 0 ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
+    sgm_select_kernel<NP, G><<<p.H, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.D, p.uniq, umagic,
+                                                             p.lr_max_diff, p.subpixel, p.fb, depth, dbg);
     return cudaGetLastError();
 }
 
