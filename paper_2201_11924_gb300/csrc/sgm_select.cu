@@ -133,10 +133,11 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int 
 
         // uniqueness: (100 - u) S(d) < 100 S(d*)  <=>  S(d) < T = ceil(100 S(d*) / (100 - u)),
         // the division done as a multiply-high by umagic = floor(2^32 / (100 - u)) + 1,
-        // exact for numerators below 2^18
+        // exact for numerators below 2^18; 100 - u = 1 (no magic in 32 bits) divides by one
         bool bad = false;
         if (uniq > 0) {
-            const uint32_t T = __umulhi(100u * smin + (uint32_t)(99 - uniq), umagic);
+            const uint32_t num = 100u * smin + (uint32_t)(99 - uniq);
+            const uint32_t T = uniq == 99 ? num : __umulhi(num, umagic);
 #pragma unroll
             for (int j = 0; j < DPT; j++) {
                 const int d = d0 + j;
@@ -217,7 +218,7 @@ cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const Se
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const uint32_t umagic = p.uniq > 0 ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
+    const uint32_t umagic = (p.uniq > 0 && p.uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
     sgm_select_kernel<NP, G><<<p.H, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.D, p.uniq, umagic,
                                                              p.lr_max_diff, p.subpixel, p.fb, depth, dbg);
     return cudaGetLastError();
