@@ -106,6 +106,30 @@ __global__ void st_v4(uint4* buf, size_t n_slots, int iters)
             buf[i] = make_uint4(it, it, it, it);
 }
 
+// Latency of one dependent chain (a single warp): cycles per operation.
+template <int OP>
+__global__ void lat_kernel(uint32_t* out, long long* cyc, int iters, uint32_t seed)
+{
+    uint32_t x = seed + threadIdx.x, y = seed * 3u + 1u;
+    long long t0 = clock64();
+    for (int it = 0; it < iters; it++) x = op<OP>(x, y ^ (x & 1u));
+    long long t1 = clock64();
+    out[threadIdx.x] = x;
+    if (threadIdx.x == 0) cyc[0] = t1 - t0;
+}
+
+template <int OP>
+void lat(const char* name, uint32_t* out, long long* cyc)
+{
+    const int iters = 4096;
+    lat_kernel<OP><<<1, 32>>>(out, cyc, iters, 77u);
+    lat_kernel<OP><<<1, 32>>>(out, cyc, iters, 77u);
+    cudaDeviceSynchronize();
+    long long h = 0;
+    cudaMemcpy(&h, cyc, sizeof(long long), cudaMemcpyDeviceToHost);
+    printf("latency %-22s %6.1f cycles\n", name, (double)h / iters);
+}
+
 void mem_probe(int nsm)
 {
     const size_t bytes = 32u << 20;   // 32 MiB: stays in L2
@@ -185,6 +209,13 @@ int main()
     run<25>("min.u16x2 + prmt", nsm, out, cyc, 2);
     run<27>("min.u16x2 + mad.lo.u32", nsm, out, cyc, 2);
     run<21>("redux.sync.min", nsm, out, cyc);
+    lat<1>("min.u32", out, cyc);
+    lat<2>("min.u16x2", out, cyc);
+    lat<4>("prmt", out, cyc);
+    lat<0>("add.u32", out, cyc);
+    lat<6>("shfl.bfly", out, cyc);
+    lat<21>("redux.sync.min", out, cyc);
+    lat<5>("popc", out, cyc);
     mem_probe(nsm);
     cudaFree(out);
     cudaFree(cyc);

@@ -19,8 +19,8 @@
 //   3. stores L(p, .) as bytes (L <= nbits + P2 <= 255) into the path volume,
 //      layout [y][x][r][Dp] so that the selection kernel reads one pixel's
 //      paths contiguously;
-//   4. forms m = min_d L(p, d): a min.u16x2 over the lane's pairs, then the
-//      group minimum with redux.sync.
+//   4. forms m = min_d L(p, d): a min.u16x2 over the lane's pairs, then a
+//      shuffle butterfly over the group.
 // The scanlines of a warp may differ in length (diagonals); the warp runs to
 // the longest and the lanes of a finished scanline stop loading and storing.
 // Padded disparities carry cost 255 in the cost volume (see cost.cu).  The
@@ -95,25 +95,36 @@ __device__ __forceinline__ uint64_t keep_policy()
     return pol;
 }
 
+// Loads the 2*NP cost bytes at p into r when pred holds, else leaves r as it
+// is.  The predicate sits inside the asm and r is a read-write operand, so
+// the load writes the ring registers directly and nothing waits for it until
+// the ring slot is unpacked PF steps later (a load into a temporary followed
+// by a conditional move would wait for the data at once).
 template <int NP>
-__device__ __forceinline__ Raw<NP> load_raw(const uint8_t* p, uint64_t pol)
+__device__ __forceinline__ void load_raw(Raw<NP>& r, const uint8_t* p, uint64_t pol, bool pred)
 {
-    Raw<NP> r;
     if constexpr (NP == 1) {
-        unsigned short v;
-        asm volatile("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(p), "l"(pol));
-        r.w[0] = v;
+        asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 h;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+                     "@q ld.global.nc.L2::cache_hint.b16 h, [%1], %3;\n\t"
+                     "@q cvt.u32.u16 %0, h;\n\t}"
+                     : "+r"(r.w[0]) : "l"(p), "r"((int)pred), "l"(pol));
     } else if constexpr (NP == 2) {
-        asm volatile("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(r.w[0]) : "l"(p), "l"(pol));
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+                     "@q ld.global.nc.L2::cache_hint.b32 %0, [%1], %3;\n\t}"
+                     : "+r"(r.w[0]) : "l"(p), "r"((int)pred), "l"(pol));
     } else if constexpr (NP == 3) {
-        const unsigned short* q = reinterpret_cast<const unsigned short*>(p);
-        r.w[0] = (uint32_t)__ldg(q) | ((uint32_t)__ldg(q + 1) << 16);
-        r.w[1] = __ldg(q + 2);
+        asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 a, b, c;\n\tsetp.ne.b32 q, %3, 0;\n\t"
+                     "@q ld.global.nc.L2::cache_hint.b16 a, [%2], %4;\n\t"
+                     "@q ld.global.nc.L2::cache_hint.b16 b, [%2+2], %4;\n\t"
+                     "@q ld.global.nc.L2::cache_hint.b16 c, [%2+4], %4;\n\t"
+                     "@q mov.b32 %0, {a, b};\n\t"
+                     "@q cvt.u32.u16 %1, c;\n\t}"
+                     : "+r"(r.w[0]), "+r"(r.w[1]) : "l"(p), "r"((int)pred), "l"(pol));
     } else {
-        asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0, %1}, [%2], %3;"
-                     : "=r"(r.w[0]), "=r"(r.w[1]) : "l"(p), "l"(pol));
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t"
+                     "@q ld.global.nc.L2::cache_hint.v2.b32 {%0, %1}, [%2], %4;\n\t}"
+                     : "+r"(r.w[0]), "+r"(r.w[1]) : "l"(p), "r"((int)pred), "l"(pol));
     }
-    return r;
 }
 
 template <int NP>
@@ -141,16 +152,18 @@ __device__ __forceinline__ void store_pairs(uint8_t* p, const uint32_t (&L)[NP])
 }
 
 // (m, m) with m the minimum over the group's cells: the lane minimum is
-// duplicated into both halves, so the 32-bit group minimum of redux.sync is
-// the pair minimum as well.
-template <int NP>
-__device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NP], unsigned gmask)
+// duplicated into both halves, then a shuffle butterfly over the G lanes of
+// the group (measured faster here than redux.sync with a partial-warp mask).
+template <int NP, int G>
+__device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NP])
 {
     uint32_t mn = L[0];
 #pragma unroll
     for (int k = 1; k < NP; k++) mn = vmin2(mn, L[k]);
     mn = vmin2(mn, __byte_perm(mn, 0, 0x1032));
-    return __reduce_min_sync(gmask, mn);
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) mn = vmin2(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    return mn;
 }
 
 // G lanes walk one scanline (32 / G scanlines per warp), each holding NP pairs.
@@ -175,7 +188,6 @@ sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, in
     const int len = scan_start(scan, rx, ry, W, H, x, y);
     const int n = SPW > 1 ? (int)__reduce_max_sync(0xffffffffu, (unsigned)len) : len;
     if (n == 0) return;                       // uniform across the warp
-    const unsigned gmask = SPW > 1 ? (((1u << G) - 1u) << ((lane / G) * G)) : 0xffffffffu;
 
     const uint32_t p1 = (uint32_t)P1 * 0x10001u;
     const uint32_t p2 = (uint32_t)P2 * 0x10001u;
@@ -190,7 +202,7 @@ sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, in
     Raw<NP> ring[PF] = {};
 #pragma unroll
     for (int k = 0; k < PF; k++) {
-        if (k < len) ring[k] = load_raw<NP>(cf, pol);
+        load_raw<NP>(ring[k], cf, pol, k < len);
         cf += cstep;
     }
     // L' = 0 and m' = 0 before the entry pixel make the recurrence return
@@ -207,7 +219,7 @@ sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, in
             if (i >= n) break;                 // uniform
             uint32_t Cp[NP];
             unpack<NP>(ring[k], Cp);
-            if (i + PF < len) ring[k] = load_raw<NP>(cf, pol);
+            load_raw<NP>(ring[k], cf, pol, i + PF < len);
             cf += cstep;
             uint32_t lo = __shfl_up_sync(0xffffffffu, Lp[NP - 1], 1, G);
             uint32_t hi = __shfl_down_sync(0xffffffffu, Lp[0], 1, G);
@@ -226,7 +238,7 @@ sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, in
             }
             if (i < len) store_pairs<NP>(op, Lp);
             op += ostep;
-            mm = group_min<NP>(Lp, gmask);
+            mm = group_min<NP, G>(Lp);
             cap = mm + p2;
         }
     }

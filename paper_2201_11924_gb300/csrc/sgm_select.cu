@@ -22,46 +22,51 @@
 namespace simsense {
 namespace {
 
-constexpr int kSelThreads = 1024;
+constexpr int kSelThreads = 512;
 constexpr int kSelWarps = kSelThreads / 32;
 
 // The lane's DPT bytes of one path, as words (2*NP bytes).
 template <int NP>
 struct Words { uint32_t w[(NP + 1) / 2]; };
 
+// Loads the lane's bytes of one path when pred holds.  The predicate sits in
+// the asm with the words as read-write operands, so the load lands in the
+// buffer registers directly and is waited for only when the buffer is summed.
 template <int NP>
-__device__ __forceinline__ Words<NP> load_words(const uint8_t* p)
+__device__ __forceinline__ void load_words(Words<NP>& r, const uint8_t* p, bool pred)
 {
-    Words<NP> r;
-    if constexpr (NP == 1) {
-        r.w[0] = __ldcs(reinterpret_cast<const unsigned short*>(p));
-    } else if constexpr (NP == 2) {
-        r.w[0] = __ldcs(reinterpret_cast<const unsigned int*>(p));
-    } else if constexpr (NP == 3) {
-        const unsigned short* q = reinterpret_cast<const unsigned short*>(p);
-        r.w[0] = (uint32_t)__ldcs(q) | ((uint32_t)__ldcs(q + 1) << 16);
-        r.w[1] = __ldcs(q + 2);
+    static_assert(NP == 3 || NP == 4, "lane groups hold 6 or 8 disparities");
+    if constexpr (NP == 3) {
+        asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 a, b, c;\n\tsetp.ne.b32 q, %3, 0;\n\t"
+                     "@q ld.global.cs.b16 a, [%2];\n\t"
+                     "@q ld.global.cs.b16 b, [%2+2];\n\t"
+                     "@q ld.global.cs.b16 c, [%2+4];\n\t"
+                     "@q mov.b32 %0, {a, b};\n\t"
+                     "@q cvt.u32.u16 %1, c;\n\t}"
+                     : "+r"(r.w[0]), "+r"(r.w[1]) : "l"(p), "r"((int)pred));
     } else {
-        uint2 v = __ldcs(reinterpret_cast<const uint2*>(p));
-        r.w[0] = v.x;
-        r.w[1] = v.y;
+        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t"
+                     "@q ld.global.cs.v2.b32 {%0, %1}, [%2];\n\t}"
+                     : "+r"(r.w[0]), "+r"(r.w[1]) : "l"(p), "r"((int)pred));
     }
-    return r;
+}
+
+template <int NP>
+__device__ __forceinline__ void load_pixel(Words<NP> (&buf)[8], const uint8_t* src, int paths, int Dp, bool act)
+{
+#pragma unroll
+    for (int r = 0; r < 8; r++) load_words<NP>(buf[r], src + r * Dp, act && r < paths);
 }
 
 // Sum of all paths for the lane's cells.  even[k] holds cells (4k, 4k+2),
 // odd[k] cells (4k+1, 4k+3) of the lane's range, as 16-bit pairs.
 template <int NP>
-__device__ __forceinline__ void sum_paths(const uint8_t* src, int paths, int Dp,
+__device__ __forceinline__ void sum_paths(const Words<NP> (&buf)[8], int paths,
                                           uint32_t (&even)[(NP + 1) / 2], uint32_t (&odd)[(NP + 1) / 2])
 {
     constexpr int NW = (NP + 1) / 2;
 #pragma unroll
     for (int k = 0; k < NW; k++) { even[k] = 0; odd[k] = 0; }
-    Words<NP> buf[8];
-#pragma unroll
-    for (int r = 0; r < 8; r++)
-        if (r < paths) buf[r] = load_words<NP>(src + r * Dp);
 #pragma unroll
     for (int r = 0; r < 8; r++) {
         if (r < paths) {
@@ -72,6 +77,97 @@ __device__ __forceinline__ void sum_paths(const uint8_t* src, int paths, int Dp,
             }
         }
     }
+}
+
+// One pixel of the row for one lane group: sum, winner, uniqueness, offers to
+// the right view, parabola.  buf holds the lane's bytes of every path.
+template <int NP, int G>
+__device__ __forceinline__ void select_pixel(const Words<NP> (&buf)[8], int x, bool act, int y, int W, int D,
+                                             int paths, int uniq, uint32_t umagic, int subpixel, int gl,
+                                             unsigned gmask, uint16_t* sw, uint32_t* keyR, float* dispf,
+                                             int16_t* dstar, uint8_t* ufail, const SelectDebug& dbg)
+{
+    constexpr int DPT = 2 * NP;
+    constexpr int Dp = G * DPT;
+    constexpr int NW = (NP + 1) / 2;
+    const int d0 = gl * DPT;
+    const size_t pix = (size_t)y * W + x;
+uint32_t even[NW], odd[NW];
+sum_paths<NP>(buf, paths, even, odd);
+    // cell j of the lane (d = d0 + j): word j/4, byte j%4
+    uint32_t S[DPT];
+#pragma unroll
+    for (int j = 0; j < DPT; j++) {
+        const uint32_t w = (j & 1) ? odd[j >> 2] : even[j >> 2];
+        S[j] = (j & 2) ? (w >> 16) : (w & 0xffffu);
+    }
+    // every cell of the group is real and matches inside the image
+    const bool interior = D == Dp && x >= Dp - 1;   // uniform per group
+    uint32_t kmin = 0xffffffffu;
+    if (interior) {
+#pragma unroll
+        for (int j = 0; j < DPT; j++) kmin = min(kmin, (S[j] << 9) | (uint32_t)(d0 + j));
+    } else {
+#pragma unroll
+        for (int j = 0; j < DPT; j++) {
+            const int d = d0 + j;
+            if (d < D) kmin = min(kmin, (S[j] << 9) | (uint32_t)d);
+        }
+    }
+    kmin = __reduce_min_sync(gmask, kmin);
+    const int ds = (int)(kmin & 511u);
+    const uint32_t smin = kmin >> 9;
+
+    // uniqueness: (100 - u) S(d) < 100 S(d*)  <=>  S(d) < T = ceil(100 S(d*) / (100 - u)),
+    // the division done as a multiply-high by umagic = floor(2^32 / (100 - u)) + 1,
+    // exact for numerators below 2^18; 100 - u = 1 (no magic in 32 bits) divides by one
+    bool bad = false;
+    if (uniq > 0) {
+        const uint32_t num = 100u * smin + (uint32_t)(99 - uniq);
+        const uint32_t T = uniq == 99 ? num : __umulhi(num, umagic);
+#pragma unroll
+        for (int j = 0; j < DPT; j++) {
+            const int d = d0 + j;
+            if ((uint32_t)(d - ds + 1) > 2u && d < D && S[j] < T) bad = true;
+        }
+    }
+    bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
+
+    if (act) {
+        if (interior) {
+#pragma unroll
+            for (int j = 0; j < DPT; j++) {
+                sw[d0 + j] = (uint16_t)S[j];
+                atomicMin(&keyR[x - d0 - j], (S[j] << 9) | (uint32_t)(d0 + j));
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < DPT; j++) {
+                const int d = d0 + j;
+                if (d < D) {
+                    sw[d] = (uint16_t)S[j];
+                    if (d <= x) atomicMin(&keyR[x - d], (S[j] << 9) | (uint32_t)d);
+                }
+            }
+        }
+        if (dbg.aggregated) {
+#pragma unroll
+            for (int j = 0; j < DPT; j++)
+                if (d0 + j < D) dbg.aggregated[pix * D + d0 + j] = (uint16_t)S[j];
+        }
+    }
+    __syncwarp();
+    if (gl == 0 && act) {
+        float df = (float)ds;
+        if (subpixel && ds >= 1 && ds <= D - 2) {
+            const int sm = sw[ds - 1], sp = sw[ds + 1], s0 = (int)smin;
+            df = (float)ds + __fdiv_rn((float)(sm - sp), (float)(2 * (sm + sp - 2 * s0)));
+        }
+        dispf[x] = df;
+        dstar[x] = (int16_t)ds;
+        ufail[x] = bad ? 1 : 0;
+    }
+    __syncwarp();
 }
 
 template <int NP, int G>
@@ -101,86 +197,20 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int 
     const size_t pstride = (size_t)paths * Dp;
     uint16_t* sw = sbuf + (warp * SPW + sub) * Dp;
     const uint8_t* row = vol + (size_t)y * W * pstride + d0;
-    for (int xb = warp * SPW; xb < W; xb += kSelWarps * SPW) {     // uniform per warp
-        const int x = xb + sub;
-        const bool act = x < W;
-        const size_t pix = (size_t)y * W + x;
-        uint32_t even[NW], odd[NW];
-        sum_paths<NP>(row + (size_t)(act ? x : 0) * pstride, paths, Dp, even, odd);
-        // cell j of the lane (d = d0 + j): word j/4, byte j%4
-        uint32_t S[DPT];
-#pragma unroll
-        for (int j = 0; j < DPT; j++) {
-            const uint32_t w = (j & 1) ? odd[j >> 2] : even[j >> 2];
-            S[j] = (j & 2) ? (w >> 16) : (w & 0xffffu);
+    constexpr int kStride = kSelWarps * SPW;   // pixels the block takes per round
+    Words<NP> bufA[8], bufB[8];
+    const int x0 = warp * SPW + sub;
+    load_pixel<NP>(bufA, row + (size_t)(x0 < W ? x0 : 0) * pstride, paths, Dp, x0 < W);
+    for (int xb = warp * SPW; xb < W; xb += 2 * kStride) {     // uniform per warp
+        const int xa = xb + sub, xbn = xa + kStride, xc = xa + 2 * kStride;
+        load_pixel<NP>(bufB, row + (size_t)(xbn < W ? xbn : 0) * pstride, paths, Dp, xbn < W);
+        select_pixel<NP, G>(bufA, xa, xa < W, y, W, D, paths, uniq, umagic, subpixel, gl, gmask, sw, keyR,
+                            dispf, dstar, ufail, dbg);
+        if (xb + kStride < W) {                                 // uniform per warp
+            load_pixel<NP>(bufA, row + (size_t)(xc < W ? xc : 0) * pstride, paths, Dp, xc < W);
+            select_pixel<NP, G>(bufB, xbn, xbn < W, y, W, D, paths, uniq, umagic, subpixel, gl, gmask, sw,
+                                keyR, dispf, dstar, ufail, dbg);
         }
-        // every cell of the group is real and matches inside the image
-        const bool interior = D == Dp && x >= Dp - 1;   // uniform per group
-        uint32_t kmin = 0xffffffffu;
-        if (interior) {
-#pragma unroll
-            for (int j = 0; j < DPT; j++) kmin = min(kmin, (S[j] << 9) | (uint32_t)(d0 + j));
-        } else {
-#pragma unroll
-            for (int j = 0; j < DPT; j++) {
-                const int d = d0 + j;
-                if (d < D) kmin = min(kmin, (S[j] << 9) | (uint32_t)d);
-            }
-        }
-        kmin = __reduce_min_sync(gmask, kmin);
-        const int ds = (int)(kmin & 511u);
-        const uint32_t smin = kmin >> 9;
-
-        // uniqueness: (100 - u) S(d) < 100 S(d*)  <=>  S(d) < T = ceil(100 S(d*) / (100 - u)),
-        // the division done as a multiply-high by umagic = floor(2^32 / (100 - u)) + 1,
-        // exact for numerators below 2^18; 100 - u = 1 (no magic in 32 bits) divides by one
-        bool bad = false;
-        if (uniq > 0) {
-            const uint32_t num = 100u * smin + (uint32_t)(99 - uniq);
-            const uint32_t T = uniq == 99 ? num : __umulhi(num, umagic);
-#pragma unroll
-            for (int j = 0; j < DPT; j++) {
-                const int d = d0 + j;
-                if ((uint32_t)(d - ds + 1) > 2u && d < D && S[j] < T) bad = true;
-            }
-        }
-        bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
-
-        if (act) {
-            if (interior) {
-#pragma unroll
-                for (int j = 0; j < DPT; j++) {
-                    sw[d0 + j] = (uint16_t)S[j];
-                    atomicMin(&keyR[x - d0 - j], (S[j] << 9) | (uint32_t)(d0 + j));
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < DPT; j++) {
-                    const int d = d0 + j;
-                    if (d < D) {
-                        sw[d] = (uint16_t)S[j];
-                        if (d <= x) atomicMin(&keyR[x - d], (S[j] << 9) | (uint32_t)d);
-                    }
-                }
-            }
-            if (dbg.aggregated) {
-#pragma unroll
-                for (int j = 0; j < DPT; j++)
-                    if (d0 + j < D) dbg.aggregated[pix * D + d0 + j] = (uint16_t)S[j];
-            }
-        }
-        __syncwarp();
-        if (gl == 0 && act) {
-            float df = (float)ds;
-            if (subpixel && ds >= 1 && ds <= D - 2) {
-                const int sm = sw[ds - 1], sp = sw[ds + 1], s0 = (int)smin;
-                df = (float)ds + __fdiv_rn((float)(sm - sp), (float)(2 * (sm + sp - 2 * s0)));
-            }
-            dispf[x] = df;
-            dstar[x] = (int16_t)ds;
-            ufail[x] = bad ? 1 : 0;
-        }
-        __syncwarp();
     }
     __syncthreads();
 
