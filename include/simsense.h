@@ -91,7 +91,7 @@ typedef struct simsense_ctx* simsense_t;
  *   uniq_ratio   0 .. 99 (percent; 0 disables the uniqueness test)
  *   lr_max_diff  < 0 disables the left-right check
  *   f, baseline  focal length in pixels and baseline in metres, both > 0
- * Limits: 1 <= D <= 256, D <= W, w <= W <= 16384 and h <= H <= 16384.
+ * Limits: 1 <= D <= 256, D <= W, w <= W <= 8192 and h <= H <= 16384.
  * Returns SIMSENSE_ERR_INVALID_ARG for anything outside these ranges,
  * SIMSENSE_ERR_OOM if the scratch memory cannot be allocated on the current
  * device (the handle is bound to that device).  On success *out owns the
@@ -196,6 +196,15 @@ int simsense_profile_read(simsense_t h, double* stage_ms, int* n_calls);
 
 /* Name of stage i (SIMSENSE_STAGE_*), or NULL. */
 const char* simsense_stage_name(int i);
+
+/*
+ * Device-side status of the handle's kernels since the last call: waits
+ * inside the kernels are bounded, and one that gives up records
+ * SIMSENSE_ERR_TIMEOUT instead of hanging (its output is then undefined).
+ * Synchronises `stream`, returns SIMSENSE_OK or the recorded status, and
+ * clears it.
+ */
+int simsense_device_status(simsense_t h, struct CUstream_st* stream);
 
 /* Bytes of device scratch memory the handle holds (for admission control). */
 size_t simsense_scratch_bytes(simsense_t h);

@@ -13,6 +13,9 @@ namespace simsense {
 constexpr int kMaxWin = 15;
 // Largest disparity range.
 constexpr int kMaxD = 256;
+// Largest image width (the selection kernel keeps per-pixel arrays of a row
+// next to its copy ring in shared memory).
+constexpr int kMaxW = 8192;
 
 struct Params {
     int W, H, D;
@@ -32,6 +35,7 @@ struct Scratch {
     void* codes_right = nullptr;
     uint8_t* cost = nullptr;       // H x W x Dp uint8, Hamming cost C
     uint8_t* paths = nullptr;      // H x W x paths x Dp uint8, L_r per path
+    int* status = nullptr;         // device status word (SIMSENSE_ERR_TIMEOUT after a bounded wait gave up)
     uint8_t* stage_left = nullptr; // host-call staging: H x W uint8
     uint8_t* stage_right = nullptr;
     float* stage_depth = nullptr;  // H x W float32
@@ -53,7 +57,7 @@ cudaError_t launch_cost(const Params& p, const void* codes_left, const void* cod
                         uint8_t* cost, cudaStream_t s);
 cudaError_t launch_paths(const Params& p, const uint8_t* cost, uint8_t* paths, cudaStream_t s);
 cudaError_t launch_select(const Params& p, const uint8_t* paths, float* depth,
-                          const SelectDebug& dbg, cudaStream_t s);
+                          const SelectDebug& dbg, int* status, cudaStream_t s);
 
 }  // namespace simsense
 

@@ -1,22 +1,27 @@
 // Selection and post-processing (arxiv 2201.11924 Sec. VI-D: best disparity
 // candidates, uniqueness test, quadratic sub-pixel fitting, left-right
-// consistency check, disparity to depth) fused into one kernel per image row.
+// consistency check, disparity to depth) fused into one kernel.
 //
-// One block per row.  A group of G lanes takes one pixel (a warp takes 32 / G
-// pixels side by side), each lane holding the same DPT consecutive
-// disparities as in the path kernel.  A
-// pixel's path costs are contiguous ([y][x][r][Dp]); a lane sums its bytes of
-// every path with two masked 32-bit adds per word (even and odd bytes as
-// packed 16-bit pairs; the sum of 8 bytes cannot carry out of a half).  Then
-//   - d* = argmin S with the smallest d on ties: warp min-reduction of the key
-//     (S << 9) | d;
-//   - the uniqueness test against every d with |d - d*| > 1;
-//   - every cell is offered to the right view: right pixel xr = x - d keeps
-//     the minimum key over the cells mapping to it (shared-memory atomicMin),
+// Blocks are persistent over image rows.  A row's path costs are one
+// contiguous run of W * paths * Dp bytes ([y][x][r][Dp]); the block streams it
+// through a ring of shared-memory stages with TMA bulk copies
+// (cp.async.bulk, completion counted on an mbarrier per stage), one thread
+// issuing the copies a few stages ahead.  A stage holds one pixel for every
+// lane group of the block (G lanes per pixel, each lane holding DPT
+// consecutive disparities as in the path kernel).  Per pixel a group
+//   - sums its bytes of every path with two masked 32-bit adds per word (even
+//     and odd bytes as packed 16-bit pairs; 8 bytes cannot carry out of a half);
+//   - finds d* = argmin S with the smallest d on ties: group min-reduction of
+//     the key (S << 9) | d;
+//   - runs the uniqueness test against every d with |d - d*| > 1;
+//   - offers every cell to the right view: right pixel xr = x - d keeps the
+//     minimum key over the cells mapping to it (shared-memory atomicMin),
 //     which is argmin_d S(xr + d, d) with ties to the smallest d;
-//   - the parabola through S(d*-1), S(d*), S(d*+1).
+//   - fits the parabola through S(d*-1), S(d*), S(d*+1).
 // When the whole row is in, each pixel's left-right check reads D_R(x - d*)
-// and the depth f*b/d_f is written.
+// and the depth f*b/d_f is written.  Every wait on a stage is bounded; a wait
+// that gives up records SIMSENSE_ERR_TIMEOUT in the status word, drains the
+// copies still in flight (again bounded) and ends the block.
 #include "internal.h"
 
 namespace simsense {
@@ -24,76 +29,95 @@ namespace {
 
 constexpr int kSelThreads = 512;
 constexpr int kSelWarps = kSelThreads / 32;
+constexpr int kMaxStages = 4;                // ring depth when shared memory allows
+constexpr uint32_t kMaxPolls = 1u << 22;     // bound on polls of one stage barrier
 
-// The lane's DPT bytes of one path, as words (2*NP bytes).
-template <int NP>
-struct Words { uint32_t w[(NP + 1) / 2]; };
-
-// Loads the lane's bytes of one path when pred holds.  The predicate sits in
-// the asm with the words as read-write operands, so the load lands in the
-// buffer registers directly and is waited for only when the buffer is summed.
-template <int NP>
-__device__ __forceinline__ void load_words(Words<NP>& r, const uint8_t* p, bool pred)
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
 {
-    static_assert(NP == 3 || NP == 4, "lane groups hold 6 or 8 disparities");
-    if constexpr (NP == 3) {
-        asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 a, b, c;\n\tsetp.ne.b32 q, %3, 0;\n\t"
-                     "@q ld.global.cs.b16 a, [%2];\n\t"
-                     "@q ld.global.cs.b16 b, [%2+2];\n\t"
-                     "@q ld.global.cs.b16 c, [%2+4];\n\t"
-                     "@q mov.b32 %0, {a, b};\n\t"
-                     "@q cvt.u32.u16 %1, c;\n\t}"
-                     : "+r"(r.w[0]), "+r"(r.w[1]) : "l"(p), "r"((int)pred));
-    } else {
-        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t"
-                     "@q ld.global.cs.v2.b32 {%0, %1}, [%2];\n\t}"
-                     : "+r"(r.w[0]), "+r"(r.w[1]) : "l"(p), "r"((int)pred));
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+// One thread: expect `bytes` on the stage barrier and start the bulk copy.
+__device__ __forceinline__ void stage_load(uint64_t* bar, void* dst, const void* src, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity)
+{
+    const uint32_t a = smem_addr(bar);
+    for (uint32_t it = 0; it < kMaxPolls; it++) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if (it > 64) __nanosleep(64);
+    }
+    return false;
+}
+
+// The lane's bytes of one path of one pixel in a stage, as words.
+template <int NP>
+__device__ __forceinline__ void lds_words(uint32_t (&w)[(NP + 1) / 2], const uint8_t* p)
+{
+    if constexpr (NP == 4) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        w[0] = v.x;
+        w[1] = v.y;
+    } else {   // NP == 3: 6 bytes, 2-byte aligned
+        const uint16_t* q = reinterpret_cast<const uint16_t*>(p);
+        w[0] = (uint32_t)q[0] | ((uint32_t)q[1] << 16);
+        w[1] = q[2];
     }
 }
 
-template <int NP>
-__device__ __forceinline__ void load_pixel(Words<NP> (&buf)[8], const uint8_t* src, int paths, int Dp, bool act)
+// Minimum of a 32-bit value over the G lanes of a group (shuffle butterfly).
+template <int G>
+__device__ __forceinline__ uint32_t group_min(uint32_t v)
 {
 #pragma unroll
-    for (int r = 0; r < 8; r++) load_words<NP>(buf[r], src + r * Dp, act && r < paths);
-}
-
-// Sum of all paths for the lane's cells.  even[k] holds cells (4k, 4k+2),
-// odd[k] cells (4k+1, 4k+3) of the lane's range, as 16-bit pairs.
-template <int NP>
-__device__ __forceinline__ void sum_paths(const Words<NP> (&buf)[8], int paths,
-                                          uint32_t (&even)[(NP + 1) / 2], uint32_t (&odd)[(NP + 1) / 2])
-{
-    constexpr int NW = (NP + 1) / 2;
-#pragma unroll
-    for (int k = 0; k < NW; k++) { even[k] = 0; odd[k] = 0; }
-#pragma unroll
-    for (int r = 0; r < 8; r++) {
-        if (r < paths) {
-#pragma unroll
-            for (int k = 0; k < NW; k++) {
-                even[k] += buf[r].w[k] & 0x00ff00ffu;
-                odd[k] += (buf[r].w[k] >> 8) & 0x00ff00ffu;
-            }
-        }
-    }
+    for (int o = 1; o < G; o <<= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
 }
 
 // One pixel of the row for one lane group: sum, winner, uniqueness, offers to
-// the right view, parabola.  buf holds the lane's bytes of every path.
+// the right view, parabola.  src is the pixel's first path in the stage.
 template <int NP, int G>
-__device__ __forceinline__ void select_pixel(const Words<NP> (&buf)[8], int x, bool act, int y, int W, int D,
+__device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act, int y, int W, int D,
                                              int paths, int uniq, uint32_t umagic, int subpixel, int gl,
-                                             unsigned gmask, uint16_t* sw, uint32_t* keyR, float* dispf,
-                                             int16_t* dstar, uint8_t* ufail, const SelectDebug& dbg)
+                                             uint16_t* sw, uint32_t* keyR, float* dispf, int16_t* dstar,
+                                             uint8_t* ufail, const SelectDebug& dbg)
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
     constexpr int NW = (NP + 1) / 2;
     const int d0 = gl * DPT;
     const size_t pix = (size_t)y * W + x;
-uint32_t even[NW], odd[NW];
-sum_paths<NP>(buf, paths, even, odd);
+    // path sums: even[k] holds cells (4k, 4k+2), odd[k] cells (4k+1, 4k+3)
+    uint32_t even[NW], odd[NW];
+#pragma unroll
+    for (int k = 0; k < NW; k++) { even[k] = 0; odd[k] = 0; }
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+        if (r < paths) {
+            uint32_t w[NW];
+            lds_words<NP>(w, src + r * Dp + d0);
+#pragma unroll
+            for (int k = 0; k < NW; k++) {
+                even[k] += w[k] & 0x00ff00ffu;
+                odd[k] += (w[k] >> 8) & 0x00ff00ffu;
+            }
+        }
+    }
     // cell j of the lane (d = d0 + j): word j/4, byte j%4
     uint32_t S[DPT];
 #pragma unroll
@@ -114,7 +138,7 @@ sum_paths<NP>(buf, paths, even, odd);
             if (d < D) kmin = min(kmin, (S[j] << 9) | (uint32_t)d);
         }
     }
-    kmin = __reduce_min_sync(gmask, kmin);
+    kmin = group_min<G>(kmin);
     const int ds = (int)(kmin & 511u);
     const uint32_t smin = kmin >> 9;
 
@@ -131,6 +155,7 @@ sum_paths<NP>(buf, paths, even, odd);
             if ((uint32_t)(d - ds + 1) > 2u && d < D && S[j] < T) bad = true;
         }
     }
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
     bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
 
     if (act) {
@@ -170,100 +195,141 @@ sum_paths<NP>(buf, paths, even, odd);
     __syncwarp();
 }
 
+// Shared-memory bytes of the block: stage ring, barriers, and per-row arrays.
 template <int NP, int G>
-__global__ void __launch_bounds__(kSelThreads)
-sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int D, int uniq, uint32_t umagic,
-                  int lr_max_diff, int subpixel, float fb, float* __restrict__ depth, SelectDebug dbg)
+size_t select_smem(int W, int paths, int stages)
+{
+    constexpr int Dp = G * 2 * NP;
+    constexpr int kPix = kSelWarps * (32 / G);
+    const size_t ring = (size_t)stages * kPix * paths * Dp;
+    return ring + 8 * kMaxStages + (size_t)W * (4 + 4 + 2 + 1) + (size_t)kPix * Dp * 2 + 64;
+}
+
+template <int NP, int G>
+__global__ void __launch_bounds__(kSelThreads, 1)
+sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int D, int uniq, uint32_t umagic,
+                  int lr_max_diff, int subpixel, float fb, float* __restrict__ depth, SelectDebug dbg,
+                  int* __restrict__ status, int kStages)
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
-    constexpr int SPW = 32 / G;               // pixels a warp takes at once
-    constexpr int NW = (NP + 1) / 2;
-    extern __shared__ __align__(16) uint8_t smem[];
-    uint32_t* keyR = reinterpret_cast<uint32_t*>(smem);              // W
-    float* dispf = reinterpret_cast<float*>(keyR + W);               // W
-    uint16_t* sbuf = reinterpret_cast<uint16_t*>(dispf + W);         // kSelWarps * SPW x Dp
-    int16_t* dstar = reinterpret_cast<int16_t*>(sbuf + kSelWarps * SPW * Dp);  // W
-    uint8_t* ufail = reinterpret_cast<uint8_t*>(dstar + W);          // W
+    constexpr int SPW = 32 / G;                 // pixels a warp takes per stage
+    constexpr int kPix = kSelWarps * SPW;       // pixels per stage
+    extern __shared__ __align__(128) uint8_t smem[];
+    const size_t pbytes = (size_t)paths * Dp;   // one pixel's path costs
+    const size_t stage_bytes = kPix * pbytes;
+    uint8_t* ring = smem;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * stage_bytes);
+    uint32_t* keyR = reinterpret_cast<uint32_t*>(bars + kMaxStages);   // W
+    float* dispf = reinterpret_cast<float*>(keyR + W);                 // W
+    uint16_t* sbuf = reinterpret_cast<uint16_t*>(dispf + W);           // kPix x Dp
+    int16_t* dstar = reinterpret_cast<int16_t*>(sbuf + kPix * Dp);     // W
+    uint8_t* ufail = reinterpret_cast<uint8_t*>(dstar + W);            // W
+    __shared__ int abort_flag;
 
-    const int y = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = lane % G, sub = lane / G;
-    const unsigned gmask = SPW > 1 ? (((1u << G) - 1u) << (sub * G)) : 0xffffffffu;
-    for (int i = threadIdx.x; i < W; i += kSelThreads) keyR[i] = 0xffffffffu;
-    __syncthreads();
-
-    const int d0 = gl * DPT;
-    const size_t pstride = (size_t)paths * Dp;
-    uint16_t* sw = sbuf + (warp * SPW + sub) * Dp;
-    const uint8_t* row = vol + (size_t)y * W * pstride + d0;
-    constexpr int kStride = kSelWarps * SPW;   // pixels the block takes per round
-    Words<NP> bufA[8], bufB[8];
-    const int x0 = warp * SPW + sub;
-    load_pixel<NP>(bufA, row + (size_t)(x0 < W ? x0 : 0) * pstride, paths, Dp, x0 < W);
-    for (int xb = warp * SPW; xb < W; xb += 2 * kStride) {     // uniform per warp
-        const int xa = xb + sub, xbn = xa + kStride, xc = xa + 2 * kStride;
-        load_pixel<NP>(bufB, row + (size_t)(xbn < W ? xbn : 0) * pstride, paths, Dp, xbn < W);
-        select_pixel<NP, G>(bufA, xa, xa < W, y, W, D, paths, uniq, umagic, subpixel, gl, gmask, sw, keyR,
-                            dispf, dstar, ufail, dbg);
-        if (xb + kStride < W) {                                 // uniform per warp
-            load_pixel<NP>(bufA, row + (size_t)(xc < W ? xc : 0) * pstride, paths, Dp, xc < W);
-            select_pixel<NP, G>(bufB, xbn, xbn < W, y, W, D, paths, uniq, umagic, subpixel, gl, gmask, sw,
-                                keyR, dispf, dstar, ufail, dbg);
-        }
+    const int slot_pix = warp * SPW + sub;      // this group's pixel within a stage
+    uint16_t* sw = sbuf + slot_pix * Dp;
+    const int nst = (W + kPix - 1) / kPix;      // stages per row
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < kStages; k++) mbar_init(&bars[k], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        abort_flag = 0;
     }
     __syncthreads();
 
-    for (int x = threadIdx.x; x < W; x += kSelThreads) {
-        const size_t pix = (size_t)y * W + x;
-        const int ds = dstar[x];
-        int m = ufail[x];
-        if (lr_max_diff >= 0) {
-            const int xr = x - ds;
-            if (xr < 0) {
-                m |= 2;
-            } else {
-                const int dr = (int)(keyR[xr] & 511u);
-                const int diff = ds > dr ? ds - dr : dr - ds;
-                if (diff > lr_max_diff) m |= 2;
+    uint32_t seq = 0;                           // stages consumed by this block so far
+    for (int y = blockIdx.x; y < H; y += gridDim.x) {
+        const uint8_t* rowsrc = vol + (size_t)y * W * pbytes;
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < kStages && k < nst; k++) {
+                const int x0 = k * kPix, n = min(kPix, W - x0);
+                stage_load(&bars[(seq + k) % kStages], ring + ((seq + k) % kStages) * stage_bytes,
+                           rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
             }
         }
-        const float df = dispf[x];
-        if (!(df > 0.0f)) m |= 4;
-        depth[pix] = m == 0 ? __fdiv_rn(fb, df) : 0.0f;
-        if (dbg.disparity_int) dbg.disparity_int[pix] = (int16_t)ds;
-        if (dbg.disparity) dbg.disparity[pix] = m == 0 ? df : -1.0f;
-        if (dbg.mask) dbg.mask[pix] = (uint8_t)m;
+        for (int i = threadIdx.x; i < W; i += kSelThreads) keyR[i] = 0xffffffffu;
+        __syncthreads();
+        for (int st = 0; st < nst; st++, seq++) {
+            const int k = seq % kStages;
+            if (!stage_wait(&bars[k], (seq / kStages) & 1u)) abort_flag = 1;
+            const int x = st * kPix + slot_pix;
+            select_pixel<NP, G>(ring + k * stage_bytes + slot_pix * pbytes, x, x < W, y, W, D, paths, uniq,
+                                umagic, subpixel, gl, sw, keyR, dispf, dstar, ufail, dbg);
+            __syncthreads();                    // everyone is done with slot k
+            if (abort_flag) {
+                if (threadIdx.x == 0) {
+                    if (status) atomicExch(status, SIMSENSE_ERR_TIMEOUT);
+                    // drain the copies still in flight into this block's ring (bounded)
+                    for (int j = 1; j < kStages && st + j < nst; j++)
+                        stage_wait(&bars[(seq + j) % kStages], ((seq + j) / kStages) & 1u);
+                }
+                return;
+            }
+            if (threadIdx.x == 0 && st + kStages < nst) {
+                const int x0 = (st + kStages) * kPix, n = min(kPix, W - x0);
+                stage_load(&bars[k], ring + k * stage_bytes, rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
+            }
+        }
+        for (int x = threadIdx.x; x < W; x += kSelThreads) {
+            const size_t pix = (size_t)y * W + x;
+            const int ds = dstar[x];
+            int m = ufail[x];
+            if (lr_max_diff >= 0) {
+                const int xr = x - ds;
+                if (xr < 0) {
+                    m |= 2;
+                } else {
+                    const int dr = (int)(keyR[xr] & 511u);
+                    const int diff = ds > dr ? ds - dr : dr - ds;
+                    if (diff > lr_max_diff) m |= 2;
+                }
+            }
+            const float df = dispf[x];
+            if (!(df > 0.0f)) m |= 4;
+            depth[pix] = m == 0 ? __fdiv_rn(fb, df) : 0.0f;
+            if (dbg.disparity_int) dbg.disparity_int[pix] = (int16_t)ds;
+            if (dbg.disparity) dbg.disparity[pix] = m == 0 ? df : -1.0f;
+            if (dbg.mask) dbg.mask[pix] = (uint8_t)m;
+        }
+        __syncthreads();                        // the row arrays are reused by the next row
     }
 }
 
 template <int NP, int G>
-cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const SelectDebug& dbg,
+cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const SelectDebug& dbg, int* status,
                      cudaStream_t s)
 {
-    // keyR + dispf + dstar + ufail per pixel of the row, one S row per pixel group
-    const size_t smem = (size_t)p.W * (4 + 4 + 2 + 1) + (size_t)kSelWarps * (32 / G) * p.Dp * 2 + 16;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(sgm_select_kernel<NP, G>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
+    int dev = 0, nsm = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    int stages = kMaxStages;                    // the deepest ring that fits
+    while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > (size_t)optin) stages--;
+    const size_t smem = select_smem<NP, G>(p.W, p.paths, stages);
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(sgm_select_kernel<NP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = p.H < nsm ? p.H : nsm;     // persistent over rows, one block per SM
     const uint32_t umagic = (p.uniq > 0 && p.uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
-    sgm_select_kernel<NP, G><<<p.H, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.D, p.uniq, umagic,
-                                                             p.lr_max_diff, p.subpixel, p.fb, depth, dbg);
+    sgm_select_kernel<NP, G><<<grid, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.H, p.D, p.uniq, umagic,
+                                                             p.lr_max_diff, p.subpixel, p.fb, depth, dbg, status,
+                                                             stages);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_select(const Params& p, const uint8_t* paths, float* depth, const SelectDebug& dbg,
-                          cudaStream_t s)
+                          int* status, cudaStream_t s)
 {
     switch (p.Dp) {                            // the path kernel's lane groups
-        case 64: return launch_t<4, 8>(p, paths, depth, dbg, s);
-        case 128: return launch_t<4, 16>(p, paths, depth, dbg, s);
-        case 192: return launch_t<3, 32>(p, paths, depth, dbg, s);
-        case 256: return launch_t<4, 32>(p, paths, depth, dbg, s);
+        case 64: return launch_t<4, 8>(p, paths, depth, dbg, status, s);
+        case 128: return launch_t<4, 16>(p, paths, depth, dbg, status, s);
+        case 192: return launch_t<3, 32>(p, paths, depth, dbg, status, s);
+        case 256: return launch_t<4, 32>(p, paths, depth, dbg, status, s);
         default: return cudaErrorInvalidValue;
     }
 }

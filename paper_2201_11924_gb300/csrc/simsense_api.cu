@@ -37,6 +37,7 @@ void free_scratch(Scratch& s)
     cudaFree(s.codes_right);
     cudaFree(s.cost);
     cudaFree(s.paths);
+    cudaFree(s.status);
     cudaFree(s.stage_left);
     cudaFree(s.stage_right);
     cudaFree(s.stage_depth);
@@ -86,7 +87,7 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
         sd.mask = dbg->mask;
     }
     e = mark(h, SIMSENSE_STAGE_SELECT, false, st);
-    if (e == cudaSuccess) e = launch_select(p, s.paths, depth, sd, st);
+    if (e == cudaSuccess) e = launch_select(p, s.paths, depth, sd, s.status, st);
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_SELECT, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     if (h->prof.on && h->prof.count < ProfileRing::kSlots) h->prof.count++;
@@ -118,7 +119,7 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
         return SIMSENSE_ERR_INVALID_ARG;
     const int nbits = ww * wh - 1;
     if (nbits < 1 || nbits > 64) return SIMSENSE_ERR_INVALID_ARG;
-    if (W < ww || H < wh || W > (1 << 14) || H > (1 << 14)) return SIMSENSE_ERR_INVALID_ARG;
+    if (W < ww || H < wh || W > kMaxW || H > (1 << 14)) return SIMSENSE_ERR_INVALID_ARG;
     if (D < 1 || D > kMaxD || D > W) return SIMSENSE_ERR_INVALID_ARG;
     if (P1 < 0 || P2 < P1 || nbits + P2 > 255) return SIMSENSE_ERR_INVALID_ARG;
     if (paths != 4 && paths != 8) return SIMSENSE_ERR_INVALID_ARG;
@@ -150,6 +151,8 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
               cudaMalloc(&s.codes_right, code_bytes) == cudaSuccess &&
               cudaMalloc((void**)&s.cost, cost_bytes) == cudaSuccess &&
               cudaMalloc((void**)&s.paths, vol_bytes) == cudaSuccess &&
+              cudaMalloc((void**)&s.status, sizeof(int)) == cudaSuccess &&
+              cudaMemset(s.status, 0, sizeof(int)) == cudaSuccess &&
               cudaMalloc((void**)&s.stage_left, npx) == cudaSuccess &&
               cudaMalloc((void**)&s.stage_right, npx) == cudaSuccess &&
               cudaMalloc((void**)&s.stage_depth, npx * sizeof(float)) == cudaSuccess;
@@ -260,6 +263,20 @@ const char* simsense_stage_name(int i)
         case SIMSENSE_STAGE_SELECT: return "select";
         default: return nullptr;
     }
+}
+
+int simsense_device_status(simsense_t h, struct CUstream_st* stream)
+{
+    if (!h) return SIMSENSE_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    int v = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&v, h->s.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && v != 0) e = cudaMemsetAsync(h->s.status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    return v == 0 ? SIMSENSE_OK : v;
 }
 
 size_t simsense_scratch_bytes(simsense_t h)

@@ -73,7 +73,7 @@ int fill_params(Params& p, int W, int H, int D, int census_win, int P1, int P2, 
         return SIMSENSE_ERR_INVALID_ARG;
     const int nbits = ww * wh - 1;
     if (nbits < 1 || nbits > 64) return SIMSENSE_ERR_INVALID_ARG;
-    if (W < ww || H < wh || W > (1 << 14) || H > (1 << 14)) return SIMSENSE_ERR_INVALID_ARG;
+    if (W < ww || H < wh || W > kMaxW || H > (1 << 14)) return SIMSENSE_ERR_INVALID_ARG;
     if (D < 1 || D > kMaxD || D > W) return SIMSENSE_ERR_INVALID_ARG;
     if (P1 < 0 || P2 < P1 || nbits + P2 > 255) return SIMSENSE_ERR_INVALID_ARG;
     if (paths != 4 && paths != 8) return SIMSENSE_ERR_INVALID_ARG;
@@ -129,6 +129,6 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
     if (e == cudaSuccess) e = launch_cost(p, codes_left, codes_right, cost, st);
     if (e == cudaSuccess) e = launch_paths(p, cost, vol, st);
     SelectDebug none{};
-    if (e == cudaSuccess) e = launch_select(p, vol, depth_f32, none, st);
+    if (e == cudaSuccess) e = launch_select(p, vol, depth_f32, none, nullptr, st);
     return e == cudaSuccess ? SIMSENSE_OK : SIMSENSE_ERR_CUDA;
 }

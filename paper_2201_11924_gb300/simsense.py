@@ -66,6 +66,8 @@ def load():
             lib.simsense_last_cuda_error.argtypes = [P]
             lib.simsense_profile_read.argtypes = [P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I)]
             lib.simsense_profile_read.restype = ctypes.c_int
+            lib.simsense_device_status.argtypes = [P, P]
+            lib.simsense_device_status.restype = ctypes.c_int
             lib.simsense_stage_name.argtypes = [I]
             lib.simsense_stage_name.restype = ctypes.c_char_p
             for fn in ("simsense_create", "simsense_compute", "simsense_compute_host",
@@ -139,6 +141,10 @@ class SimSense:
         n = ctypes.c_int()
         self._check(load().simsense_profile_read(self.handle, ms, ctypes.byref(n)), "simsense_profile_read")
         return {STAGES[i]: float(ms[i]) for i in range(len(STAGES))}, int(n.value)
+
+    def device_status(self, stream=None) -> int:
+        """Synchronise and return (then clear) the kernels' device status code."""
+        return int(load().simsense_device_status(self.handle, _stream_ptr(stream)))
 
     def scratch_bytes(self) -> int:
         return int(load().simsense_scratch_bytes(self.handle))

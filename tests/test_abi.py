@@ -61,6 +61,7 @@ def test_strerror(lib):
     (64, 32, 16, 5 | (5 << 8), 7, 86, 8, 0, 1, 0.0, 0.055),        # f
     (64, 32, 16, 5 | (5 << 8), 7, 86, 8, 0, 1, 300.0, -1.0),       # baseline
     (4, 32, 4, 5 | (5 << 8), 7, 86, 8, 0, 1, 300.0, 0.055),        # W < window
+    (8193, 32, 64, 5 | (5 << 8), 7, 86, 8, 0, 1, 300.0, 0.055),    # W above the row limit
 ])
 def test_create_rejects_bad_arguments(lib, args):
     h = ctypes.c_void_p()

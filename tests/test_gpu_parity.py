@@ -33,6 +33,7 @@ def _run(lib, wl, left, right, aggregated=True):
         out = m.compute_debug(lt, rt, aggregated=aggregated)
         depth2 = m.compute(lt, rt)
         torch.cuda.synchronize()
+        assert m.device_status() == 0     # no bounded device-side wait gave up
         res = {k: v.cpu().numpy() for k, v in out.items()}
         res["depth_plain"] = depth2.cpu().numpy()
     return res
