@@ -152,8 +152,9 @@ __device__ __forceinline__ void store_pairs(uint8_t* p, const uint32_t (&L)[NP])
 }
 
 // (m, m) with m the minimum over the group's cells: the lane minimum is
-// duplicated into both halves, then a shuffle butterfly over the G lanes of
-// the group (measured faster here than redux.sync with a partial-warp mask).
+// duplicated into both halves, then reduced over the group: one redux.sync
+// for a whole warp, a shuffle butterfly for a partial-warp group (measured
+// faster here than redux.sync with a partial mask).
 template <int NP, int G>
 __device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NP])
 {
@@ -161,9 +162,13 @@ __device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NP])
 #pragma unroll
     for (int k = 1; k < NP; k++) mn = vmin2(mn, L[k]);
     mn = vmin2(mn, __byte_perm(mn, 0, 0x1032));
+    if constexpr (G == 32) {
+        return __reduce_min_sync(0xffffffffu, mn);
+    } else {
 #pragma unroll
-    for (int o = 1; o < G; o <<= 1) mn = vmin2(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-    return mn;
+        for (int o = 1; o < G; o <<= 1) mn = vmin2(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        return mn;
+    }
 }
 
 // G lanes walk one scanline (32 / G scanlines per warp), each holding NP pairs.
@@ -171,16 +176,12 @@ __device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NP])
 // i % PF, a static index inside the PF-times unrolled loop), which hides the
 // DRAM latency behind PF steps of the recurrence.
 template <int NP, int G, int PF>
-__global__ void __launch_bounds__(kPathThreads)
-sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, int paths,
-                 uint8_t* __restrict__ vol)
+__device__ __forceinline__ void walk(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, int paths,
+                                     uint8_t* __restrict__ vol, int r, int rx, int ry)
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
     constexpr int SPW = 32 / G;
-    const int r = blockIdx.y;
-    int rx, ry;
-    path_dir(r, rx, ry);
     const int lane = threadIdx.x & 31;
     const int gl = lane % G;
     const int scan = (blockIdx.x * (kPathThreads / 32) + (threadIdx.x >> 5)) * SPW + lane / G;
@@ -244,14 +245,35 @@ sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, in
     }
 }
 
-template <int NP, int G>
+// The horizontal directions have the longest scanlines (W steps of a
+// recurrence that is inherently sequential), so they decide the kernel's
+// critical path: they are walked by whole warps (NPH pairs per lane, group
+// minimum by one redux.sync, the shortest step latency measured).  The other
+// directions are throughput-bound and use G-lane groups with NP pairs.
+template <int NP, int G, int NPH, int PF>
+__global__ void __launch_bounds__(kPathThreads)
+sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, int paths,
+                 uint8_t* __restrict__ vol)
+{
+    static_assert(G * 2 * NP == 32 * 2 * NPH, "both layouts cover the same padded range");
+    const int r = blockIdx.y;
+    int rx, ry;
+    path_dir(r, rx, ry);
+    if (ry == 0) walk<NPH, 32, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry);
+    else walk<NP, G, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry);
+}
+
+template <int NP, int G, int NPH>
 cudaError_t launch_t(const Params& p, const uint8_t* C, uint8_t* vol, cudaStream_t s)
 {
     constexpr int PF = 8;
-    const int nscan = p.W + p.H - 1;          // the most scanlines any direction has
+    // blocks: enough for the non-horizontal directions (W + H - 1 scanlines at
+    // most, 32/G per warp) and for the horizontal ones (H scanlines, 1 per warp)
     const int per_block = (kPathThreads / 32) * (32 / G);
-    dim3 grid((nscan + per_block - 1) / per_block, p.paths);
-    sgm_paths_kernel<NP, G, PF><<<grid, kPathThreads, 0, s>>>(C, p.W, p.H, p.P1, p.P2, p.paths, vol);
+    const int nb = (p.W + p.H - 1 + per_block - 1) / per_block;
+    const int nbh = (p.H + kPathThreads / 32 - 1) / (kPathThreads / 32);
+    dim3 grid(nb > nbh ? nb : nbh, p.paths);
+    sgm_paths_kernel<NP, G, NPH, PF><<<grid, kPathThreads, 0, s>>>(C, p.W, p.H, p.P1, p.P2, p.paths, vol);
     return cudaGetLastError();
 }
 
@@ -260,10 +282,10 @@ cudaError_t launch_t(const Params& p, const uint8_t* C, uint8_t* vol, cudaStream
 cudaError_t launch_paths(const Params& p, const uint8_t* C, uint8_t* paths, cudaStream_t s)
 {
     switch (p.Dp) {                            // lanes per scanline x 8 (or 6) disparities per lane
-        case 64: return launch_t<4, 8>(p, C, paths, s);
-        case 128: return launch_t<4, 16>(p, C, paths, s);
-        case 192: return launch_t<3, 32>(p, C, paths, s);
-        case 256: return launch_t<4, 32>(p, C, paths, s);
+        case 64: return launch_t<4, 8, 1>(p, C, paths, s);
+        case 128: return launch_t<4, 16, 2>(p, C, paths, s);
+        case 192: return launch_t<3, 32, 3>(p, C, paths, s);
+        case 256: return launch_t<4, 32, 4>(p, C, paths, s);
         default: return cudaErrorInvalidValue;
     }
 }

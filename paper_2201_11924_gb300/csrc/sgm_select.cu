@@ -100,7 +100,11 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
     constexpr int NW = (NP + 1) / 2;
-    const int d0 = gl * DPT;
+    // With two groups per warp, the second one takes its disparity chunks
+    // rotated by half a group, so that the two groups' shared-memory reads of
+    // their two pixels fall on disjoint banks.
+    const int chunk = G == 16 ? (gl + 8 * ((threadIdx.x & 31) / 16)) % 16 : gl;
+    const int d0 = chunk * DPT;
     const size_t pix = (size_t)y * W + x;
     // path sums: even[k] holds cells (4k, 4k+2), odd[k] cells (4k+1, 4k+3)
     uint32_t even[NW], odd[NW];
@@ -206,7 +210,7 @@ size_t select_smem(int W, int paths, int stages)
 }
 
 template <int NP, int G>
-__global__ void __launch_bounds__(kSelThreads, 1)
+__global__ void __launch_bounds__(kSelThreads, 2)
 sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int D, int uniq, uint32_t umagic,
                   int lr_max_diff, int subpixel, float fb, float* __restrict__ depth, SelectDebug dbg,
                   int* __restrict__ status, int kStages)
@@ -301,18 +305,27 @@ template <int NP, int G>
 cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const SelectDebug& dbg, int* status,
                      cudaStream_t s)
 {
-    int dev = 0, nsm = 0, optin = 0;
+    int dev = 0, nsm = 0, optin = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    int stages = kMaxStages;                    // the deepest ring that fits
-    while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > (size_t)optin) stages--;
+    // two blocks per SM with the deepest ring that lets both fit, else one
+    // block per SM with up to kMaxStages stages
+    int blocks_per_sm = 2, stages = kMaxStages;
+    const size_t half = (size_t)per_sm / 2 - 1024;
+    while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > half) stages--;
+    if (select_smem<NP, G>(p.W, p.paths, stages) > half) {
+        blocks_per_sm = 1;
+        stages = kMaxStages;
+        while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > (size_t)optin) stages--;
+    }
     const size_t smem = select_smem<NP, G>(p.W, p.paths, stages);
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute(sgm_select_kernel<NP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = p.H < nsm ? p.H : nsm;     // persistent over rows, one block per SM
+    const int grid = p.H < blocks_per_sm * nsm ? p.H : blocks_per_sm * nsm;   // persistent over rows
     const uint32_t umagic = (p.uniq > 0 && p.uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
     sgm_select_kernel<NP, G><<<grid, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.H, p.D, p.uniq, umagic,
                                                              p.lr_max_diff, p.subpixel, p.fb, depth, dbg, status,
