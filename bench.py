@@ -55,17 +55,20 @@ def algorithmic_ops(wl):
     """Scalar integer ops per launch of each kernel (no SIMD credit).
 
     Per cell (x, y, d): the Hamming cost once (XOR, POPC on 64-bit codes:
-    5 ops; on 32-bit codes: 2), 7 ops per path for the recurrence (min of the
-    neighbours, +P1, min with L'(d), -m', min with P2, +C, the min-reduction
-    over d), then in the selection kernel the sum over the paths (1 per path)
-    and 6 for WTA, uniqueness and the right-view argmin.  The census costs
-    2 ops per bit per view and pixel."""
+    5 ops; on 32-bit codes: 2; the cost kernel), 7 ops per path for the
+    recurrence (min of the neighbours, +P1, min with L'(d), -m', min with P2,
+    +C, the min-reduction over d; the path kernel), then in the selection
+    kernel the sum over the paths (1 per path) and 6 for WTA, uniqueness and
+    the right-view argmin.  The census costs 2 ops per bit per view and
+    pixel.  The sum over the stages is the per-cell count cost + 8 P + 6 +
+    4 nbits / D."""
     cells = wl.W * wl.H * wl.D
     cost = 5 if wl.nbits > 32 else 2
     return {
-        "paths": cells * (cost + 7 * wl.paths),
-        "select": cells * (wl.paths + 6),
         "census": wl.W * wl.H * 4 * wl.nbits,
+        "cost": cells * cost,
+        "paths": cells * 7 * wl.paths,
+        "select": cells * (wl.paths + 6),
     }
 
 
@@ -201,6 +204,74 @@ def run_reference(args, wl):
     return 0
 
 
+def run_batchmix(args):
+    """The 64-pair batch of uneven sizes ({640x360 D64, 848x480 D96,
+    1280x720 D128, 1280x720 D256}, 7x7 census, 8 paths): frames/s of one
+    CUDA-graph launch per batch (autotuned per class) against the same pairs
+    as 64 sequential plain calls."""
+    import torch
+    from paper_2201_11924_gb300 import simsense
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    wls = configs.batch_workloads()
+    pairs = [scenes.make_pair(w) for w in wls]
+    L = [torch.from_numpy(p["left"]).to(dev) for p in pairs]
+    R = [torch.from_numpy(p["right"]).to(dev) for p in pairs]
+    Z = [torch.empty((w.H, w.W), dtype=torch.float32, device=dev) for w in wls]
+    cells = sum(w.cells for w in wls)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    # plain: one handle per size class, 64 calls in sequence
+    handles = {}
+    for w in wls:
+        key = (w.W, w.H, w.D)
+        if key not in handles:
+            handles[key] = simsense.SimSense.from_workload(w)
+    def plain_round():
+        for i, w in enumerate(wls):
+            handles[(w.W, w.H, w.D)].compute(L[i], R[i], Z[i])
+    for _ in range(args.warmup):
+        plain_round()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plain_round()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1) / args.steps
+    for h in handles.values():
+        h.close()
+
+    with simsense.SimSenseBatch(wls) as b:
+        tuning = b.tune(L, R, Z, reps=2)
+        for _ in range(args.warmup):
+            b.compute(L, R, Z)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            b.compute(L, R, Z)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        batch_ms = ev0.elapsed_time(ev1) / args.steps
+        status = b.device_status()
+        classes = [dict(b.class_info(c)[0], pairs=b.class_info(c)[1], **tuning[c]) for c in range(b.num_classes())]
+    line = {
+        "metric": METRIC, "value": len(wls) / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "batch64_mixed_640x360D64_848x480D96_1280x720D128_1280x720D256_census7x7_8path",
+                   "pairs": len(wls), "cells_per_batch": cells, "graph": True,
+                   "l2": "no flush: every batch streams ~60 GB of path volumes through HBM"},
+        "cells_per_s": cells / (batch_ms / 1e3),
+        "plain_value": len(wls) / (plain_ms / 1e3), "plain_ms_per_batch": plain_ms,
+        "speedup_vs_plain": plain_ms / batch_ms, "classes": classes, "device_status": status,
+        "gpu_launches": 4 * len(classes) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,12 +282,18 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-strip-rows", type=int, default=90)
+    ap.add_argument("--mode", default="plain", choices=["plain", "batchmix"],
+                    help="plain: the default contract line; batchmix: the 64-pair mixed batch")
+    ap.add_argument("--batch-pairs", type=int, default=8,
+                    help="pairs per batch for the batched sub-measurement of the plain workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = configs.ALL[args.workload]
 
     if args.impl == "reference":
         return run_reference(args, wl)
+    if args.mode == "batchmix":
+        return run_batchmix(args)
 
     import torch
     from paper_2201_11924_gb300 import simsense
@@ -295,6 +372,38 @@ def main():
            "h2d_bytes_per_step": 2 * wl.W * wl.H, "d2h_bytes_per_step": 4 * wl.W * wl.H,
            "steps": e2e_steps}
 
+    # the batched form on the same workload: batch_pairs pairs per CUDA-graph launch
+    batched = None
+    if args.batch_pairs > 1:
+        nb = args.batch_pairs
+        bwl = [wl] * nb
+        bl = [lefts[i % n_pairs] for i in range(nb)]
+        br = [rights[i % n_pairs] for i in range(nb)]
+        bd = [torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev) for _ in range(nb)]
+        with simsense.SimSenseBatch(bwl) as bt:
+            for _ in range(args.warmup):
+                bt.compute(bl, br, bd)
+            torch.cuda.synchronize()
+            bsteps = max(3, args.steps // nb)
+            if dist:
+                dist.barrier()
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            for _ in range(bsteps):
+                bt.compute(bl, br, bd)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            b_ms = b0.elapsed_time(b1)
+            status = bt.device_status()
+        if dist:
+            t = torch.tensor([b_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            b_ms = float(t.item())
+        batched = {"value": world * nb * bsteps / (b_ms / 1e3), "unit": UNIT, "pairs_per_batch": nb,
+                   "batches": bsteps, "ms_per_batch": b_ms / bsteps, "graph": True,
+                   "device_status": status}
+
     if rank != 0:
         m.close()
         if dist:
@@ -334,7 +443,8 @@ def main():
                          "far above the 129 MB L2", "path": "plain (one pair per call)"},
         "cells_per_s": value * wl.cells,
         "e2e": e2e,
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 4 * args.steps,
+        "batched": batched,
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,

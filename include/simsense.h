@@ -212,6 +212,82 @@ size_t simsense_scratch_bytes(simsense_t h);
 /* Release the handle and its scratch memory.  NULL is accepted. */
 int simsense_destroy(simsense_t h);
 
+/* ------------------------------------------------------------------ batches */
+
+/*
+ * Parameters of one pair of a batch: the arguments of simsense_create (same
+ * ranges) plus the sub-pixel switch (0/1).
+ */
+typedef struct simsense_pair_params {
+    int W, H, D;
+    int census_win;          /* SIMSENSE_WIN(w, h) */
+    int P1, P2;
+    int paths;               /* 4 or 8 */
+    int uniq_ratio;          /* 0 .. 99 */
+    int lr_max_diff;         /* < 0 disables */
+    int subpixel;            /* 0 or 1 */
+    float f, baseline;
+} simsense_pair_params_t;
+
+typedef struct simsense_batch* simsense_batch_t;
+
+#define SIMSENSE_BATCH_OPT_GRAPH    1     /* 1 (default): capture/replay a CUDA graph; 0: launch directly */
+
+/*
+ * A batch of n pairs of possibly different sizes, disparity ranges and
+ * parameters, computed together (the same four stages as simsense_compute,
+ * each stage one launch per class of pairs with identical parameters, the
+ * classes running concurrently).  Allocates all scratch memory once, on the
+ * current device.  Errors as simsense_create.
+ */
+int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* pairs, int n);
+
+/*
+ * Depth of every pair of the batch.  left, right, depth: HOST arrays of n
+ * DEVICE pointers (pair i: H_i x W_i uint8 views, H_i x W_i float32 depth).
+ * Asynchronous on stream.  The first call records the work into a CUDA graph
+ * and later calls with the same pointers replay it (new pointers re-record).
+ */
+int simsense_batch_compute(simsense_batch_t b, const uint8_t* const* left, const uint8_t* const* right,
+                           float* const* depth, struct CUstream_st* stream);
+
+/* Set a batch option (SIMSENSE_BATCH_OPT_*). */
+int simsense_batch_set_option(simsense_batch_t b, int opt, int value);
+
+/* Number of classes (groups of pairs with identical parameters). */
+int simsense_batch_num_classes(simsense_batch_t b);
+
+/* Parameters and pair count of class c; either pointer may be NULL. */
+int simsense_batch_class_info(simsense_batch_t b, int c, simsense_pair_params_t* params, int* npairs);
+
+/*
+ * Launch choices of class c: prefetch = cost words in flight per scanline of
+ * the path kernel (4, 8 or 12), select_blocks = selection-kernel blocks per
+ * SM (1 or 2).  Results do not depend on them.
+ */
+int simsense_batch_get_tuning(simsense_batch_t b, int c, int* prefetch, int* select_blocks);
+int simsense_batch_set_tuning(simsense_batch_t b, int c, int prefetch, int select_blocks);
+
+/*
+ * Autotuner: for every class, runs its stages with each candidate launch
+ * choice `reps` times (1 .. 100) on the given buffers, timed with CUDA
+ * events on `stream`, and keeps the fastest.  Synchronises the stream.
+ */
+int simsense_batch_tune(simsense_batch_t b, const uint8_t* const* left, const uint8_t* const* right,
+                        float* const* depth, int reps, struct CUstream_st* stream);
+
+/* Device scratch bytes held by the batch. */
+size_t simsense_batch_scratch_bytes(simsense_batch_t b);
+
+/* As simsense_device_status, for a batch. */
+int simsense_batch_device_status(simsense_batch_t b, struct CUstream_st* stream);
+
+/* CUDA error code behind the batch's last SIMSENSE_ERR_CUDA. */
+int simsense_batch_last_cuda_error(simsense_batch_t b);
+
+/* Release the batch and its memory.  NULL is accepted. */
+int simsense_batch_destroy(simsense_batch_t b);
+
 /* Static description of a status code. */
 const char* simsense_strerror(int code);
 

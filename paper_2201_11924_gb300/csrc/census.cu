@@ -16,14 +16,19 @@ constexpr int kTY = 8;
 constexpr int kTileW = kTX + kMaxWin - 1;
 constexpr int kTileH = kTY + kMaxWin - 1;
 
-template <typename CodeT>
+// WW, WH > 0: the window is a compile-time constant and the loops unroll;
+// WW = WH = 0: the window comes from ww, wh at run time.
+// blockIdx.z = 2 * pair + view (0 = left, 1 = right).
+template <typename CodeT, int WW, int WH, int N>
 __global__ void __launch_bounds__(kTX * kTY)
-census_kernel(const uint8_t* __restrict__ left, const uint8_t* __restrict__ right, int W, int H,
-              int ww, int wh, CodeT* __restrict__ out_left, CodeT* __restrict__ out_right)
+census_kernel(PairTable<N> pt, int W, int H, int ww_rt, int wh_rt)
 {
     __shared__ uint8_t tile[kTileH * kTileW];
-    const uint8_t* img = blockIdx.z ? right : left;
-    CodeT* out = blockIdx.z ? out_right : out_left;
+    const int ww = WW > 0 ? WW : ww_rt;
+    const int wh = WH > 0 ? WH : wh_rt;
+    const PairPtrs& pp = pt.p[blockIdx.z >> 1];
+    const uint8_t* img = (blockIdx.z & 1) ? pp.right : pp.left;
+    CodeT* out = static_cast<CodeT*>((blockIdx.z & 1) ? pp.codes_right : pp.codes_left);
     const int rx = ww >> 1, ry = wh >> 1;
     const int tw = kTX + 2 * rx, th = kTY + 2 * ry;
     const int gx0 = blockIdx.x * kTX - rx, gy0 = blockIdx.y * kTY - ry;
@@ -39,10 +44,21 @@ census_kernel(const uint8_t* __restrict__ left, const uint8_t* __restrict__ righ
     const uint8_t* t = tile + threadIdx.y * kTileW + threadIdx.x;
     const uint8_t c = t[ry * kTileW + rx];
     CodeT code = 0;
-    for (int dy = 0; dy < wh; dy++) {
-        for (int dx = 0; dx < ww; dx++) {
-            if (dy == ry && dx == rx) continue;
-            code = (code << 1) | (CodeT)(t[dy * kTileW + dx] < c ? 1u : 0u);
+    if constexpr (WW > 0) {
+#pragma unroll
+        for (int dy = 0; dy < WH; dy++) {
+#pragma unroll
+            for (int dx = 0; dx < WW; dx++) {
+                if (dy == WH / 2 && dx == WW / 2) continue;
+                code = (code << 1) | (CodeT)(t[dy * kTileW + dx] < c ? 1u : 0u);
+            }
+        }
+    } else {
+        for (int dy = 0; dy < wh; dy++) {
+            for (int dx = 0; dx < ww; dx++) {
+                if (dy == ry && dx == rx) continue;
+                code = (code << 1) | (CodeT)(t[dy * kTileW + dx] < c ? 1u : 0u);
+            }
         }
     }
     out[(size_t)y * W + x] = code;
@@ -54,20 +70,37 @@ __global__ void widen_kernel(const uint32_t* __restrict__ in, uint64_t* __restri
     if (i < n) out[i] = in[i];
 }
 
+template <int N>
+cudaError_t census_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
+{
+    PairTable<N> pt{};
+    for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
+    dim3 block(kTX, kTY);
+    dim3 grid((p.W + kTX - 1) / kTX, (p.H + kTY - 1) / kTY, 2 * n);
+    const int w = p.win_w, h = p.win_h;
+    if (w == 7 && h == 7)
+        census_kernel<uint64_t, 7, 7, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
+    else if (w == 9 && h == 7)
+        census_kernel<uint64_t, 9, 7, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
+    else if (w == 5 && h == 5)
+        census_kernel<uint32_t, 5, 5, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
+    else if (p.wide_codes)
+        census_kernel<uint64_t, 0, 0, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
+    else
+        census_kernel<uint32_t, 0, 0, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_census(const Params& p, const uint8_t* left, const uint8_t* right,
-                          void* codes_left, void* codes_right, cudaStream_t s)
+cudaError_t launch_census(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
 {
-    dim3 block(kTX, kTY);
-    dim3 grid((p.W + kTX - 1) / kTX, (p.H + kTY - 1) / kTY, 2);
-    if (p.wide_codes)
-        census_kernel<uint64_t><<<grid, block, 0, s>>>(left, right, p.W, p.H, p.win_w, p.win_h,
-                                                       (uint64_t*)codes_left, (uint64_t*)codes_right);
-    else
-        census_kernel<uint32_t><<<grid, block, 0, s>>>(left, right, p.W, p.H, p.win_w, p.win_h,
-                                                       (uint32_t*)codes_left, (uint32_t*)codes_right);
-    return cudaGetLastError();
+    for (int b = 0; b < n; b += kMaxBatch) {
+        const int c = n - b < kMaxBatch ? n - b : kMaxBatch;
+        cudaError_t e = c == 1 ? census_chunk<1>(p, pairs + b, 1, s) : census_chunk<kMaxBatch>(p, pairs + b, c, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_widen_codes(const Params& p, const void* codes, uint64_t* out, cudaStream_t s)

@@ -27,14 +27,18 @@ constexpr int kCostThreads = 256;
 __device__ __forceinline__ uint32_t popc(uint32_t v) { return __popc(v); }
 __device__ __forceinline__ uint32_t popc(uint64_t v) { return __popcll(v); }
 
-template <typename CodeT, int DPT>
+// blockIdx.z = pair.
+template <typename CodeT, int DPT, int N>
 __global__ void __launch_bounds__(kCostThreads)
-cost_kernel(const CodeT* __restrict__ cL, const CodeT* __restrict__ cR, int W, int D, int nbits,
-            uint8_t* __restrict__ C)
+cost_kernel(PairTable<N> pt, int W, int D, int nbits)
 {
     constexpr int Dp = 32 * DPT;
     __shared__ CodeT sR[kCostPix + Dp];
     __shared__ CodeT sL[kCostPix];
+    const PairPtrs& pp = pt.p[blockIdx.z];
+    const CodeT* __restrict__ cL = static_cast<const CodeT*>(pp.codes_left);
+    const CodeT* __restrict__ cR = static_cast<const CodeT*>(pp.codes_right);
+    uint8_t* __restrict__ C = pp.cost;
     const int y = blockIdx.y, x0 = blockIdx.x * kCostPix;
     const CodeT* rowL = cL + (size_t)y * W;
     const CodeT* rowR = cR + (size_t)y * W;
@@ -71,29 +75,39 @@ cost_kernel(const CodeT* __restrict__ cL, const CodeT* __restrict__ cR, int W, i
     }
 }
 
-template <typename CodeT>
-cudaError_t launch_code(const Params& p, const void* cl, const void* cr, uint8_t* C, cudaStream_t s)
+template <typename CodeT, int N>
+cudaError_t cost_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
 {
-    dim3 grid((p.W + kCostPix - 1) / kCostPix, p.H);
-    const CodeT* a = (const CodeT*)cl;
-    const CodeT* b = (const CodeT*)cr;
+    PairTable<N> pt{};
+    for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
+    dim3 grid((p.W + kCostPix - 1) / kCostPix, p.H, n);
     switch (p.dpt) {
-        case 2: cost_kernel<CodeT, 2><<<grid, kCostThreads, 0, s>>>(a, b, p.W, p.D, p.nbits, C); break;
-        case 4: cost_kernel<CodeT, 4><<<grid, kCostThreads, 0, s>>>(a, b, p.W, p.D, p.nbits, C); break;
-        case 6: cost_kernel<CodeT, 6><<<grid, kCostThreads, 0, s>>>(a, b, p.W, p.D, p.nbits, C); break;
-        case 8: cost_kernel<CodeT, 8><<<grid, kCostThreads, 0, s>>>(a, b, p.W, p.D, p.nbits, C); break;
+        case 2: cost_kernel<CodeT, 2, N><<<grid, kCostThreads, 0, s>>>(pt, p.W, p.D, p.nbits); break;
+        case 4: cost_kernel<CodeT, 4, N><<<grid, kCostThreads, 0, s>>>(pt, p.W, p.D, p.nbits); break;
+        case 6: cost_kernel<CodeT, 6, N><<<grid, kCostThreads, 0, s>>>(pt, p.W, p.D, p.nbits); break;
+        case 8: cost_kernel<CodeT, 8, N><<<grid, kCostThreads, 0, s>>>(pt, p.W, p.D, p.nbits); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
 
+template <int N>
+cudaError_t cost_code(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
+{
+    if (p.wide_codes) return cost_chunk<uint64_t, N>(p, pairs, n, s);
+    return cost_chunk<uint32_t, N>(p, pairs, n, s);
+}
+
 }  // namespace
 
-cudaError_t launch_cost(const Params& p, const void* codes_left, const void* codes_right, uint8_t* C,
-                        cudaStream_t s)
+cudaError_t launch_cost(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
 {
-    if (p.wide_codes) return launch_code<uint64_t>(p, codes_left, codes_right, C, s);
-    return launch_code<uint32_t>(p, codes_left, codes_right, C, s);
+    for (int b = 0; b < n; b += kMaxBatch) {
+        const int c = n - b < kMaxBatch ? n - b : kMaxBatch;
+        cudaError_t e = c == 1 ? cost_code<1>(p, pairs + b, 1, s) : cost_code<kMaxBatch>(p, pairs + b, c, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace simsense

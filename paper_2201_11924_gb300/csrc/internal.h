@@ -42,6 +42,34 @@ struct Scratch {
     size_t bytes = 0;
 };
 
+// Device buffers of one pair (one stereo pair of a batch, or the single pair
+// of a plain call).
+struct PairPtrs {
+    const uint8_t* left;
+    const uint8_t* right;
+    void* codes_left;        // H x W uint32 or uint64
+    void* codes_right;
+    uint8_t* cost;           // H x W x Dp
+    uint8_t* vol;            // H x W x paths x Dp
+    float* depth;            // H x W
+};
+
+// Pairs of one launch, passed by value as a kernel parameter (nothing to
+// upload per call; a captured graph keeps it).  Kernels take the pair index
+// from the grid.
+constexpr int kMaxBatch = 32;
+template <int N>
+struct PairTable {
+    PairPtrs p[N];
+};
+
+// Launch choices the autotuner may change (defaults are the measured best
+// for 1280x720, D = 128 on GB300).
+struct Tuning {
+    int prefetch = 8;        // path kernel: cost words in flight per scanline (4, 8 or 12)
+    int select_blocks = 2;   // selection kernel: blocks per SM (1 or 2)
+};
+
 // Optional outputs of the selection kernel (device pointers, may be null).
 struct SelectDebug {
     uint16_t* aggregated;
@@ -50,14 +78,19 @@ struct SelectDebug {
     uint8_t* mask;
 };
 
-cudaError_t launch_census(const Params& p, const uint8_t* left, const uint8_t* right,
-                          void* codes_left, void* codes_right, cudaStream_t s);
+// Each launcher runs one stage for pairs[0 .. n-1], all with parameters p
+// (n > kMaxBatch is split into several launches).
+cudaError_t launch_census(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s);
 cudaError_t launch_widen_codes(const Params& p, const void* codes, uint64_t* out, cudaStream_t s);
-cudaError_t launch_cost(const Params& p, const void* codes_left, const void* codes_right,
-                        uint8_t* cost, cudaStream_t s);
-cudaError_t launch_paths(const Params& p, const uint8_t* cost, uint8_t* paths, cudaStream_t s);
-cudaError_t launch_select(const Params& p, const uint8_t* paths, float* depth,
+cudaError_t launch_cost(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s);
+cudaError_t launch_paths(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s);
+cudaError_t launch_select(const Params& p, const PairPtrs* pairs, int n, const Tuning& t,
                           const SelectDebug& dbg, int* status, cudaStream_t s);
+
+// Validation and derived fields shared by every entry point that takes a
+// parameter set (the ranges of simsense_create).
+int make_params(Params& p, int W, int H, int D, int census_win, int P1, int P2, int paths,
+                int uniq_ratio, int lr_max_diff, float f, float baseline, int subpixel);
 
 }  // namespace simsense
 

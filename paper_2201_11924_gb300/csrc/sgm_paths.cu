@@ -250,12 +250,13 @@ __device__ __forceinline__ void walk(const uint8_t* __restrict__ C, int W, int H
 // critical path: they are walked by whole warps (NPH pairs per lane, group
 // minimum by one redux.sync, the shortest step latency measured).  The other
 // directions are throughput-bound and use G-lane groups with NP pairs.
-template <int NP, int G, int NPH, int PF>
+template <int NP, int G, int NPH, int PF, int N>
 __global__ void __launch_bounds__(kPathThreads)
-sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, int paths,
-                 uint8_t* __restrict__ vol)
+sgm_paths_kernel(PairTable<N> pt, int W, int H, int P1, int P2, int paths)
 {
     static_assert(G * 2 * NP == 32 * 2 * NPH, "both layouts cover the same padded range");
+    const uint8_t* __restrict__ C = pt.p[blockIdx.z].cost;      // blockIdx.z = pair
+    uint8_t* __restrict__ vol = pt.p[blockIdx.z].vol;
     const int r = blockIdx.y;
     int rx, ry;
     path_dir(r, rx, ry);
@@ -263,31 +264,53 @@ sgm_paths_kernel(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, in
     else walk<NP, G, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry);
 }
 
-template <int NP, int G, int NPH>
-cudaError_t launch_t(const Params& p, const uint8_t* C, uint8_t* vol, cudaStream_t s)
+template <int NP, int G, int NPH, int PF, int N>
+cudaError_t paths_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
 {
-    constexpr int PF = 8;
+    PairTable<N> pt{};
+    for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
     // blocks: enough for the non-horizontal directions (W + H - 1 scanlines at
     // most, 32/G per warp) and for the horizontal ones (H scanlines, 1 per warp)
     const int per_block = (kPathThreads / 32) * (32 / G);
     const int nb = (p.W + p.H - 1 + per_block - 1) / per_block;
     const int nbh = (p.H + kPathThreads / 32 - 1) / (kPathThreads / 32);
-    dim3 grid(nb > nbh ? nb : nbh, p.paths);
-    sgm_paths_kernel<NP, G, NPH, PF><<<grid, kPathThreads, 0, s>>>(C, p.W, p.H, p.P1, p.P2, p.paths, vol);
+    dim3 grid(nb > nbh ? nb : nbh, p.paths, n);
+    sgm_paths_kernel<NP, G, NPH, PF, N><<<grid, kPathThreads, 0, s>>>(pt, p.W, p.H, p.P1, p.P2, p.paths);
     return cudaGetLastError();
+}
+
+template <int NP, int G, int NPH, int N>
+cudaError_t paths_pf(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s)
+{
+    switch (t.prefetch) {
+        case 4: return paths_chunk<NP, G, NPH, 4, N>(p, pairs, n, s);
+        case 12: return paths_chunk<NP, G, NPH, 12, N>(p, pairs, n, s);
+        default: return paths_chunk<NP, G, NPH, 8, N>(p, pairs, n, s);
+    }
+}
+
+template <int N>
+cudaError_t paths_dp(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s)
+{
+    switch (p.Dp) {                            // lanes per scanline x 8 (or 6) disparities per lane
+        case 64: return paths_pf<4, 8, 1, N>(p, pairs, n, t, s);
+        case 128: return paths_pf<4, 16, 2, N>(p, pairs, n, t, s);
+        case 192: return paths_pf<3, 32, 3, N>(p, pairs, n, t, s);
+        case 256: return paths_pf<4, 32, 4, N>(p, pairs, n, t, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_paths(const Params& p, const uint8_t* C, uint8_t* paths, cudaStream_t s)
+cudaError_t launch_paths(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s)
 {
-    switch (p.Dp) {                            // lanes per scanline x 8 (or 6) disparities per lane
-        case 64: return launch_t<4, 8, 1>(p, C, paths, s);
-        case 128: return launch_t<4, 16, 2>(p, C, paths, s);
-        case 192: return launch_t<3, 32, 3>(p, C, paths, s);
-        case 256: return launch_t<4, 32, 4>(p, C, paths, s);
-        default: return cudaErrorInvalidValue;
+    for (int b = 0; b < n; b += kMaxBatch) {
+        const int c = n - b < kMaxBatch ? n - b : kMaxBatch;
+        cudaError_t e = c == 1 ? paths_dp<1>(p, pairs + b, 1, t, s) : paths_dp<kMaxBatch>(p, pairs + b, c, t, s);
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 }  // namespace simsense

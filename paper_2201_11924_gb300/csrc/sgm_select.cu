@@ -209,11 +209,12 @@ size_t select_smem(int W, int paths, int stages)
     return ring + 8 * kMaxStages + (size_t)W * (4 + 4 + 2 + 1) + (size_t)kPix * Dp * 2 + 64;
 }
 
-template <int NP, int G>
+// Items are (pair, row); blocks are persistent over them.
+template <int NP, int G, int N>
 __global__ void __launch_bounds__(kSelThreads, 2)
-sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int D, int uniq, uint32_t umagic,
-                  int lr_max_diff, int subpixel, float fb, float* __restrict__ depth, SelectDebug dbg,
-                  int* __restrict__ status, int kStages)
+sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, int uniq, uint32_t umagic,
+                  int lr_max_diff, int subpixel, float fb, SelectDebug dbg, int* __restrict__ status,
+                  int kStages)
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
@@ -244,8 +245,10 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int 
     __syncthreads();
 
     uint32_t seq = 0;                           // stages consumed by this block so far
-    for (int y = blockIdx.x; y < H; y += gridDim.x) {
-        const uint8_t* rowsrc = vol + (size_t)y * W * pbytes;
+    for (int item = blockIdx.x; item < npairs * H; item += gridDim.x) {
+        const int pair = item / H, y = item - pair * H;
+        const uint8_t* rowsrc = pt.p[pair].vol + (size_t)y * W * pbytes;
+        float* __restrict__ depth = pt.p[pair].depth;
         if (threadIdx.x == 0) {
             for (int k = 0; k < kStages && k < nst; k++) {
                 const int x0 = k * kPix, n = min(kPix, W - x0);
@@ -301,50 +304,67 @@ sgm_select_kernel(const uint8_t* __restrict__ vol, int paths, int W, int H, int 
     }
 }
 
-template <int NP, int G>
-cudaError_t launch_t(const Params& p, const uint8_t* vol, float* depth, const SelectDebug& dbg, int* status,
-                     cudaStream_t s)
+template <int NP, int G, int N>
+cudaError_t select_chunk(const Params& p, const PairPtrs* pairs, int n, const Tuning& t,
+                         const SelectDebug& dbg, int* status, cudaStream_t s)
 {
+    PairTable<N> pt{};
+    for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
     int dev = 0, nsm = 0, optin = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    // two blocks per SM with the deepest ring that lets both fit, else one
-    // block per SM with up to kMaxStages stages
-    int blocks_per_sm = 2, stages = kMaxStages;
-    const size_t half = (size_t)per_sm / 2 - 1024;
-    while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > half) stages--;
-    if (select_smem<NP, G>(p.W, p.paths, stages) > half) {
-        blocks_per_sm = 1;
-        stages = kMaxStages;
-        while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > (size_t)optin) stages--;
+    // t.select_blocks blocks per SM with the deepest ring that lets them fit,
+    // else one block per SM with up to kMaxStages stages
+    int blocks_per_sm = t.select_blocks == 1 ? 1 : 2, stages = kMaxStages;
+    if (blocks_per_sm == 2) {
+        const size_t half = (size_t)per_sm / 2 - 1024;
+        while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > half) stages--;
+        if (select_smem<NP, G>(p.W, p.paths, stages) > half) blocks_per_sm = 1, stages = kMaxStages;
     }
+    if (blocks_per_sm == 1)
+        while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > (size_t)optin) stages--;
     const size_t smem = select_smem<NP, G>(p.W, p.paths, stages);
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(sgm_select_kernel<NP, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(sgm_select_kernel<NP, G, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = p.H < blocks_per_sm * nsm ? p.H : blocks_per_sm * nsm;   // persistent over rows
+    const int items = n * p.H;
+    const int grid = items < blocks_per_sm * nsm ? items : blocks_per_sm * nsm;   // persistent over rows
     const uint32_t umagic = (p.uniq > 0 && p.uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
-    sgm_select_kernel<NP, G><<<grid, kSelThreads, smem, s>>>(vol, p.paths, p.W, p.H, p.D, p.uniq, umagic,
-                                                             p.lr_max_diff, p.subpixel, p.fb, depth, dbg, status,
-                                                             stages);
+    sgm_select_kernel<NP, G, N><<<grid, kSelThreads, smem, s>>>(pt, n, p.paths, p.W, p.H, p.D, p.uniq, umagic,
+                                                                p.lr_max_diff, p.subpixel, p.fb, dbg, status,
+                                                                stages);
     return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t select_dp(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, const SelectDebug& dbg,
+                      int* status, cudaStream_t s)
+{
+    switch (p.Dp) {                            // the path kernel's lane groups
+        case 64: return select_chunk<4, 8, N>(p, pairs, n, t, dbg, status, s);
+        case 128: return select_chunk<4, 16, N>(p, pairs, n, t, dbg, status, s);
+        case 192: return select_chunk<3, 32, N>(p, pairs, n, t, dbg, status, s);
+        case 256: return select_chunk<4, 32, N>(p, pairs, n, t, dbg, status, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
-cudaError_t launch_select(const Params& p, const uint8_t* paths, float* depth, const SelectDebug& dbg,
+cudaError_t launch_select(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, const SelectDebug& dbg,
                           int* status, cudaStream_t s)
 {
-    switch (p.Dp) {                            // the path kernel's lane groups
-        case 64: return launch_t<4, 8>(p, paths, depth, dbg, status, s);
-        case 128: return launch_t<4, 16>(p, paths, depth, dbg, status, s);
-        case 192: return launch_t<3, 32>(p, paths, depth, dbg, status, s);
-        case 256: return launch_t<4, 32>(p, paths, depth, dbg, status, s);
-        default: return cudaErrorInvalidValue;
+    for (int b = 0; b < n; b += kMaxBatch) {
+        const int c = n - b < kMaxBatch ? n - b : kMaxBatch;
+        const SelectDebug none{};
+        cudaError_t e = c == 1 ? select_dp<1>(p, pairs + b, 1, t, n == 1 ? dbg : none, status, s)
+                               : select_dp<kMaxBatch>(p, pairs + b, c, t, none, status, s);
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 }  // namespace simsense

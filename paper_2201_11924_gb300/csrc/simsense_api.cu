@@ -67,16 +67,18 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
 {
     const Params& p = h->p;
     Scratch& s = h->s;
+    const PairPtrs pair{left, right, s.codes_left, s.codes_right, s.cost, s.paths, depth};
+    const Tuning tune{};
     cudaError_t e = mark(h, SIMSENSE_STAGE_CENSUS, false, st);
-    if (e == cudaSuccess) e = launch_census(p, left, right, s.codes_left, s.codes_right, st);
+    if (e == cudaSuccess) e = launch_census(p, &pair, 1, st);
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_CENSUS, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     e = mark(h, SIMSENSE_STAGE_COST, false, st);
-    if (e == cudaSuccess) e = launch_cost(p, s.codes_left, s.codes_right, s.cost, st);
+    if (e == cudaSuccess) e = launch_cost(p, &pair, 1, st);
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_COST, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     e = mark(h, SIMSENSE_STAGE_PATHS, false, st);
-    if (e == cudaSuccess) e = launch_paths(p, s.cost, s.paths, st);
+    if (e == cudaSuccess) e = launch_paths(p, &pair, 1, tune, st);
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_PATHS, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     SelectDebug sd{};
@@ -87,7 +89,7 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
         sd.mask = dbg->mask;
     }
     e = mark(h, SIMSENSE_STAGE_SELECT, false, st);
-    if (e == cudaSuccess) e = launch_select(p, s.paths, depth, sd, s.status, st);
+    if (e == cudaSuccess) e = launch_select(p, &pair, 1, tune, sd, s.status, st);
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_SELECT, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     if (h->prof.on && h->prof.count < ProfileRing::kSlots) h->prof.count++;
@@ -104,13 +106,11 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
 
 }  // namespace
 
-extern "C" {
+namespace simsense {
 
-int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1, int P2,
-                    int paths, int uniq_ratio, int lr_max_diff, float f, float baseline)
+int make_params(Params& p, int W, int H, int D, int census_win, int P1, int P2, int paths, int uniq_ratio,
+                int lr_max_diff, float f, float baseline, int subpixel)
 {
-    if (!out) return SIMSENSE_ERR_INVALID_ARG;
-    *out = nullptr;
     const int ww = census_win & 0xff;
     int wh = (census_win >> 8) & 0xff;
     if (wh == 0) wh = ww;
@@ -124,22 +124,39 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
     if (P1 < 0 || P2 < P1 || nbits + P2 > 255) return SIMSENSE_ERR_INVALID_ARG;
     if (paths != 4 && paths != 8) return SIMSENSE_ERR_INVALID_ARG;
     if (uniq_ratio < 0 || uniq_ratio > 99) return SIMSENSE_ERR_INVALID_ARG;
+    if (subpixel != 0 && subpixel != 1) return SIMSENSE_ERR_INVALID_ARG;
     if (!(f > 0.0f) || !(baseline > 0.0f) || !isfinite(f) || !isfinite(baseline))
         return SIMSENSE_ERR_INVALID_ARG;
-
-    simsense_ctx* h = new (std::nothrow) simsense_ctx();
-    if (!h) return SIMSENSE_ERR_OOM;
-    Params& p = h->p;
+    p = Params{};
     p.W = W; p.H = H; p.D = D;
     p.win_w = ww; p.win_h = wh; p.nbits = nbits;
     p.P1 = P1; p.P2 = P2; p.paths = paths;
     p.uniq = uniq_ratio; p.lr_max_diff = lr_max_diff;
-    p.subpixel = 1;
+    p.subpixel = subpixel;
     p.f = f; p.baseline = baseline;
     p.fb = (float)((double)f * (double)baseline);
     p.dpt = 2 * ((D + 63) / 64);
     p.Dp = 32 * p.dpt;
     p.wide_codes = nbits > 32;
+    return SIMSENSE_OK;
+}
+
+}  // namespace simsense
+
+extern "C" {
+
+int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1, int P2,
+                    int paths, int uniq_ratio, int lr_max_diff, float f, float baseline)
+{
+    if (!out) return SIMSENSE_ERR_INVALID_ARG;
+    *out = nullptr;
+    Params pv;
+    const int rc = make_params(pv, W, H, D, census_win, P1, P2, paths, uniq_ratio, lr_max_diff, f, baseline, 1);
+    if (rc != SIMSENSE_OK) return rc;
+    simsense_ctx* h = new (std::nothrow) simsense_ctx();
+    if (!h) return SIMSENSE_ERR_OOM;
+    Params& p = h->p;
+    p = pv;
     if (cudaGetDevice(&h->device) != cudaSuccess) { delete h; return SIMSENSE_ERR_CUDA; }
 
     const size_t npx = (size_t)W * H;

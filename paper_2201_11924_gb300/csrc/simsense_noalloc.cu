@@ -22,8 +22,6 @@
 //    written earlier in that same call, so leftovers of a previous call are
 //    harmless;
 //  - problems whose scratch does not fit are rejected.
-#include <math.h>
-
 #include <mutex>
 
 #include "internal.h"
@@ -61,39 +59,6 @@ int scratch_address(void** out)
 
 size_t round256(size_t v) { return (v + 255) & ~(size_t)255; }
 
-// The argument ranges of simsense_create, applied to a per-call parameter set.
-int fill_params(Params& p, int W, int H, int D, int census_win, int P1, int P2, int paths,
-                int uniq_ratio, int lr_max_diff, float f, float baseline, int subpixel)
-{
-    const int ww = census_win & 0xff;
-    int wh = (census_win >> 8) & 0xff;
-    if (wh == 0) wh = ww;
-    if ((census_win >> 16) != 0) return SIMSENSE_ERR_INVALID_ARG;
-    if (ww < 1 || wh < 1 || ww > kMaxWin || wh > kMaxWin || !(ww & 1) || !(wh & 1))
-        return SIMSENSE_ERR_INVALID_ARG;
-    const int nbits = ww * wh - 1;
-    if (nbits < 1 || nbits > 64) return SIMSENSE_ERR_INVALID_ARG;
-    if (W < ww || H < wh || W > kMaxW || H > (1 << 14)) return SIMSENSE_ERR_INVALID_ARG;
-    if (D < 1 || D > kMaxD || D > W) return SIMSENSE_ERR_INVALID_ARG;
-    if (P1 < 0 || P2 < P1 || nbits + P2 > 255) return SIMSENSE_ERR_INVALID_ARG;
-    if (paths != 4 && paths != 8) return SIMSENSE_ERR_INVALID_ARG;
-    if (uniq_ratio < 0 || uniq_ratio > 99) return SIMSENSE_ERR_INVALID_ARG;
-    if (subpixel != 0 && subpixel != 1) return SIMSENSE_ERR_INVALID_ARG;
-    if (!(f > 0.0f) || !(baseline > 0.0f) || !isfinite(f) || !isfinite(baseline))
-        return SIMSENSE_ERR_INVALID_ARG;
-    p.W = W; p.H = H; p.D = D;
-    p.win_w = ww; p.win_h = wh; p.nbits = nbits;
-    p.P1 = P1; p.P2 = P2; p.paths = paths;
-    p.uniq = uniq_ratio; p.lr_max_diff = lr_max_diff;
-    p.subpixel = subpixel;
-    p.f = f; p.baseline = baseline;
-    p.fb = (float)((double)f * (double)baseline);
-    p.dpt = 2 * ((D + 63) / 64);
-    p.Dp = 32 * p.dpt;
-    p.wide_codes = nbits > 32;
-    return SIMSENSE_OK;
-}
-
 }  // namespace
 
 extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* right_u8,
@@ -104,8 +69,7 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
 {
     if (!left_u8 || !right_u8 || !depth_f32) return SIMSENSE_ERR_INVALID_ARG;
     Params p{};
-    int rc = fill_params(p, W, H, D, census_win, P1, P2, paths, uniq_ratio, lr_max_diff, f, baseline,
-                         subpixel);
+    int rc = make_params(p, W, H, D, census_win, P1, P2, paths, uniq_ratio, lr_max_diff, f, baseline, subpixel);
     if (rc != SIMSENSE_OK) return rc;
 
     // carve the fixed array: left codes | right codes | cost volume | path volume
@@ -125,10 +89,12 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
     uint8_t* vol = cost + cost_bytes;
 
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = launch_census(p, left_u8, right_u8, codes_left, codes_right, st);
-    if (e == cudaSuccess) e = launch_cost(p, codes_left, codes_right, cost, st);
-    if (e == cudaSuccess) e = launch_paths(p, cost, vol, st);
-    SelectDebug none{};
-    if (e == cudaSuccess) e = launch_select(p, vol, depth_f32, none, nullptr, st);
+    const PairPtrs pair{left_u8, right_u8, codes_left, codes_right, cost, vol, depth_f32};
+    const Tuning tune{};
+    const SelectDebug none{};
+    cudaError_t e = launch_census(p, &pair, 1, st);
+    if (e == cudaSuccess) e = launch_cost(p, &pair, 1, st);
+    if (e == cudaSuccess) e = launch_paths(p, &pair, 1, tune, st);
+    if (e == cudaSuccess) e = launch_select(p, &pair, 1, tune, none, nullptr, st);
     return e == cudaSuccess ? SIMSENSE_OK : SIMSENSE_ERR_CUDA;
 }

@@ -217,3 +217,147 @@ class SimSense:
             self.close()
         except Exception:
             pass
+
+
+class PairParamsT(ctypes.Structure):
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int), ("D", ctypes.c_int), ("census_win", ctypes.c_int),
+                ("P1", ctypes.c_int), ("P2", ctypes.c_int), ("paths", ctypes.c_int), ("uniq_ratio", ctypes.c_int),
+                ("lr_max_diff", ctypes.c_int), ("subpixel", ctypes.c_int), ("f", ctypes.c_float),
+                ("baseline", ctypes.c_float)]
+
+
+BATCH_OPT_GRAPH = 1
+
+
+def _load_batch():
+    lib = load()
+    if not getattr(lib, "_batch_ready", False):
+        P, I = ctypes.c_void_p, ctypes.c_int
+        PP = ctypes.POINTER(ctypes.c_void_p)
+        lib.simsense_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(PairParamsT), I]
+        lib.simsense_batch_compute.argtypes = [P, PP, PP, PP, P]
+        lib.simsense_batch_set_option.argtypes = [P, I, I]
+        lib.simsense_batch_num_classes.argtypes = [P]
+        lib.simsense_batch_class_info.argtypes = [P, I, ctypes.POINTER(PairParamsT), ctypes.POINTER(I)]
+        lib.simsense_batch_get_tuning.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
+        lib.simsense_batch_set_tuning.argtypes = [P, I, I, I]
+        lib.simsense_batch_tune.argtypes = [P, PP, PP, PP, I, P]
+        lib.simsense_batch_scratch_bytes.argtypes = [P]
+        lib.simsense_batch_scratch_bytes.restype = ctypes.c_size_t
+        lib.simsense_batch_device_status.argtypes = [P, P]
+        lib.simsense_batch_last_cuda_error.argtypes = [P]
+        lib.simsense_batch_destroy.argtypes = [P]
+        for fn in ("simsense_batch_create", "simsense_batch_compute", "simsense_batch_set_option",
+                   "simsense_batch_num_classes", "simsense_batch_class_info", "simsense_batch_get_tuning",
+                   "simsense_batch_set_tuning", "simsense_batch_tune", "simsense_batch_device_status",
+                   "simsense_batch_last_cuda_error", "simsense_batch_destroy"):
+            getattr(lib, fn).restype = ctypes.c_int
+        lib._batch_ready = True
+    return lib
+
+
+def pair_params(wl) -> PairParamsT:
+    return PairParamsT(wl.W, wl.H, wl.D, wl.win_w | (wl.win_h << 8), wl.P1, wl.P2, wl.paths, wl.uniq,
+                       wl.lr_max_diff, int(bool(wl.subpixel)), float(wl.f), float(wl.baseline))
+
+
+class SimSenseBatch:
+    """Many pairs of uneven sizes in one call (simsense_batch_*): one CUDA
+    graph of per-class launches, with per-class launch choices that
+    ``tune()`` (the native autotuner) or a tuning cache can set."""
+
+    def __init__(self, workloads):
+        lib = _load_batch()
+        self.workloads = list(workloads)
+        self.n = len(self.workloads)
+        arr = (PairParamsT * self.n)(*[pair_params(w) for w in self.workloads])
+        self._h = ctypes.c_void_p()
+        rc = lib.simsense_batch_create(ctypes.byref(self._h), arr, self.n)
+        if rc != OK:
+            self._h = None
+            raise SimsenseError(rc, "simsense_batch_create")
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise RuntimeError("SimSenseBatch handle is closed")
+        return self._h
+
+    def _check(self, rc, what):
+        if rc != OK:
+            err = _load_batch().simsense_batch_last_cuda_error(self._h) if rc == ERR_CUDA else 0
+            raise SimsenseError(rc, what, err)
+
+    def _ptrs(self, lefts, rights, depths):
+        import torch
+        n = self.n
+        if not (len(lefts) == len(rights) == len(depths) == n):
+            raise ValueError(f"expected {n} lefts, rights and depths")
+        L = (ctypes.c_void_p * n)()
+        R = (ctypes.c_void_p * n)()
+        Z = (ctypes.c_void_p * n)()
+        for i, wl in enumerate(self.workloads):
+            shape = (wl.H, wl.W)
+            L[i] = _dev_ptr(lefts[i], torch.uint8, shape, f"left[{i}]").value
+            R[i] = _dev_ptr(rights[i], torch.uint8, shape, f"right[{i}]").value
+            Z[i] = _dev_ptr(depths[i], torch.float32, shape, f"depth[{i}]").value
+        return L, R, Z
+
+    def compute(self, lefts, rights, depths, stream=None):
+        L, R, Z = self._ptrs(lefts, rights, depths)
+        self._check(_load_batch().simsense_batch_compute(self.handle, L, R, Z, _stream_ptr(stream)),
+                    "simsense_batch_compute")
+        return depths
+
+    def set_graph(self, on: bool):
+        self._check(_load_batch().simsense_batch_set_option(self.handle, BATCH_OPT_GRAPH, int(bool(on))),
+                    "simsense_batch_set_option")
+
+    def num_classes(self) -> int:
+        return int(_load_batch().simsense_batch_num_classes(self.handle))
+
+    def class_info(self, c: int):
+        prm = PairParamsT()
+        n = ctypes.c_int()
+        self._check(_load_batch().simsense_batch_class_info(self.handle, c, ctypes.byref(prm), ctypes.byref(n)),
+                    "simsense_batch_class_info")
+        return {k: getattr(prm, k) for k, _ in PairParamsT._fields_}, int(n.value)
+
+    def get_tuning(self, c: int):
+        a, b = ctypes.c_int(), ctypes.c_int()
+        self._check(_load_batch().simsense_batch_get_tuning(self.handle, c, ctypes.byref(a), ctypes.byref(b)),
+                    "simsense_batch_get_tuning")
+        return {"prefetch": int(a.value), "select_blocks": int(b.value)}
+
+    def set_tuning(self, c: int, prefetch: int, select_blocks: int):
+        self._check(_load_batch().simsense_batch_set_tuning(self.handle, c, int(prefetch), int(select_blocks)),
+                    "simsense_batch_set_tuning")
+
+    def tune(self, lefts, rights, depths, reps: int = 3, stream=None):
+        L, R, Z = self._ptrs(lefts, rights, depths)
+        self._check(_load_batch().simsense_batch_tune(self.handle, L, R, Z, int(reps), _stream_ptr(stream)),
+                    "simsense_batch_tune")
+        return [self.get_tuning(c) for c in range(self.num_classes())]
+
+    def scratch_bytes(self) -> int:
+        return int(_load_batch().simsense_batch_scratch_bytes(self.handle))
+
+    def device_status(self, stream=None) -> int:
+        return int(_load_batch().simsense_batch_device_status(self.handle, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            _load_batch().simsense_batch_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

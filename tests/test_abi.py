@@ -73,3 +73,17 @@ def test_null_handles_are_rejected(lib):
     assert lib.simsense_compute(None, None, None, None, None) == -1
     assert lib.simsense_set_option(None, 1, 0) == -1
     assert lib.simsense_destroy(None) == 0
+
+
+def test_batch_create_rejects_bad_arguments(lib):
+    from paper_2201_11924_gb300 import configs, simsense
+    blib = simsense._load_batch()
+    h = ctypes.c_void_p()
+    good = simsense.pair_params(configs.SMALL_320)
+    bad = simsense.pair_params(configs.SMALL_320.with_(D=0))
+    arr = (simsense.PairParamsT * 2)(good, bad)
+    assert blib.simsense_batch_create(ctypes.byref(h), arr, 2) == -1 and not h.value
+    assert blib.simsense_batch_create(ctypes.byref(h), arr, 0) == -1
+    assert blib.simsense_batch_create(None, arr, 1) == -1
+    assert blib.simsense_batch_destroy(None) == 0
+    assert blib.simsense_batch_num_classes(None) == -1
