@@ -272,6 +272,56 @@ def run_batchmix(args):
     return 0
 
 
+def run_serve(args):
+    """Request loop over 1024 cameras (sizes 50% 848x480 D96, 40% 1280x720
+    D128, 10% 1920x1080 D256; 7x7 census, 8 paths, uniqueness 15, L/R 1,
+    sub-pixel), Poisson arrivals: the continuous-batching server against the
+    same trace served one request at a time (the plain per-request path).
+    Latency = arrival to depth ready, including the frame upload."""
+    import torch
+    from paper_2201_11924_gb300 import serve
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    cams = [configs.serve_camera(c) for c in range(1024)]
+    frames = {}
+    for w in cams:
+        key = (w.W, w.H, w.D)
+        frames.setdefault(key, [])
+        if len(frames[key]) < 2:
+            p = scenes.make_pair(w)
+            frames[key].append((p["left"], p["right"]))
+    srv = serve.DepthServer(cams, frames, slots_per_class=args.serve_slots, device=dev)
+    mean_cells = sum(w.cells for w in cams) / len(cams)
+    out = {}
+    for name, seq in (("continuous", False), ("plain_sequential", True)):
+        # warm-up: a short trace
+        srv.run(serve.poisson_trace(len(cams), 500.0, 0.2, seed=1), sequential=seq)
+        trace = serve.poisson_trace(len(cams), args.serve_rate, args.serve_seconds, seed=5999)
+        t0 = time.perf_counter()
+        done = srv.run(trace, time_limit=args.serve_seconds + 2.0, sequential=seq)
+        wall = time.perf_counter() - t0
+        st = serve.latency_stats(done, wall)
+        st.update({"offered": len(trace), "offered_per_s": len(trace) / args.serve_seconds,
+                   "backlog_at_stop": srv.backlog, "wall_s": wall,
+                   "cells_per_s": st["served_per_s"] * mean_cells})
+        out[name] = st
+    slots = srv.slot_counts()
+    srv.close()
+    c = out["continuous"]
+    line = {
+        "metric": METRIC, "value": c["served_per_s"], "unit": UNIT, "n_gpus": 1, "steps": c["served"],
+        "warmup": 1, "ms_per_step": 1e3 / c["served_per_s"] if c["served_per_s"] else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": "serve_1024cams_poisson_50pct848x480D96_40pct1280x720D128_10pct1920x1080D256",
+                   "rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "slots": slots,
+                   "upload": True},
+        "p50_ms": c["p50_ms"], "p99_ms": c["p99_ms"], "serve": out,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,8 +332,12 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-strip-rows", type=int, default=90)
-    ap.add_argument("--mode", default="plain", choices=["plain", "batchmix"],
-                    help="plain: the default contract line; batchmix: the 64-pair mixed batch")
+    ap.add_argument("--mode", default="plain", choices=["plain", "batchmix", "serve"],
+                    help="plain: the default contract line; batchmix: the 64-pair mixed batch; "
+                         "serve: the continuous-batching request loop")
+    ap.add_argument("--serve-rate", type=float, default=4000.0, help="Poisson arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=8.0, help="trace length")
+    ap.add_argument("--serve-slots", type=int, default=4, help="compute slots per size class")
     ap.add_argument("--batch-pairs", type=int, default=8,
                     help="pairs per batch for the batched sub-measurement of the plain workload")
     args = ap.parse_args()
@@ -294,6 +348,8 @@ def main():
         return run_reference(args, wl)
     if args.mode == "batchmix":
         return run_batchmix(args)
+    if args.mode == "serve":
+        return run_serve(args)
 
     import torch
     from paper_2201_11924_gb300 import simsense
