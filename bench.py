@@ -293,17 +293,17 @@ def run_serve(args):
     srv = serve.DepthServer(cams, frames, slots_per_class=args.serve_slots, device=dev)
     mean_cells = sum(w.cells for w in cams) / len(cams)
     out = {}
-    for name, seq in (("continuous", False), ("plain_sequential", True)):
+    for name, seq in (("plain_sequential", True), ("continuous", False)):
         # warm-up: a short trace
         srv.run(serve.poisson_trace(len(cams), 500.0, 0.2, seed=1), sequential=seq)
         trace = serve.poisson_trace(len(cams), args.serve_rate, args.serve_seconds, seed=5999)
         t0 = time.perf_counter()
         done = srv.run(trace, time_limit=args.serve_seconds + 2.0, sequential=seq)
         wall = time.perf_counter() - t0
-        st = serve.latency_stats(done, wall)
+        st = serve.latency_stats(done, wall, cams)
         st.update({"offered": len(trace), "offered_per_s": len(trace) / args.serve_seconds,
-                   "backlog_at_stop": srv.backlog, "wall_s": wall,
-                   "cells_per_s": st["served_per_s"] * mean_cells})
+                   "offered_cells_per_s": len(trace) * mean_cells / args.serve_seconds,
+                   "backlog_at_stop": srv.backlog, "wall_s": wall})
         out[name] = st
     slots = srv.slot_counts()
     srv.close()

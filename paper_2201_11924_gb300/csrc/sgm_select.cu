@@ -22,6 +22,8 @@
 // and the depth f*b/d_f is written.  Every wait on a stage is bounded; a wait
 // that gives up records SIMSENSE_ERR_TIMEOUT in the status word, drains the
 // copies still in flight (again bounded) and ends the block.
+#include <mutex>
+
 #include "internal.h"
 
 namespace simsense {
@@ -304,18 +306,65 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, i
     }
 }
 
+// Device limits, read once per device.
+struct DevLimits {
+    int nsm = 0, optin = 0, per_sm = 0;
+};
+
+cudaError_t dev_limits(DevLimits& out)
+{
+    constexpr int kMaxDev = 64;
+    static DevLimits cache[kMaxDev];
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    DevLimits& c = cache[dev];
+    if (c.nsm == 0) {
+        e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) {
+            c = DevLimits{};
+            return e;
+        }
+    }
+    out = c;
+    return cudaSuccess;
+}
+
+// Raises the kernel's dynamic shared-memory limit when a launch needs more
+// than any earlier one on this device (setting it on every launch would put
+// a function-attribute call between concurrent launches of other streams).
+template <typename K>
+cudaError_t ensure_smem(K kernel, size_t bytes)
+{
+    constexpr int kMaxDev = 64;
+    static size_t set_to[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (bytes <= set_to[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) set_to[dev] = bytes;
+    return e;
+}
+
 template <int NP, int G, int N>
 cudaError_t select_chunk(const Params& p, const PairPtrs* pairs, int n, const Tuning& t,
                          const SelectDebug& dbg, int* status, cudaStream_t s)
 {
     PairTable<N> pt{};
     for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
-    int dev = 0, nsm = 0, optin = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    DevLimits lim;
+    cudaError_t e = dev_limits(lim);
     if (e != cudaSuccess) return e;
+    const int nsm = lim.nsm, optin = lim.optin, per_sm = lim.per_sm;
     // t.select_blocks blocks per SM with the deepest ring that lets them fit,
     // else one block per SM with up to kMaxStages stages
     int blocks_per_sm = t.select_blocks == 1 ? 1 : 2, stages = kMaxStages;
@@ -328,7 +377,7 @@ cudaError_t select_chunk(const Params& p, const PairPtrs* pairs, int n, const Tu
         while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > (size_t)optin) stages--;
     const size_t smem = select_smem<NP, G>(p.W, p.paths, stages);
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(sgm_select_kernel<NP, G, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = ensure_smem(sgm_select_kernel<NP, G, N>, smem);
     if (e != cudaSuccess) return e;
     const int items = n * p.H;
     const int grid = items < blocks_per_sm * nsm ? items : blocks_per_sm * nsm;   // persistent over rows

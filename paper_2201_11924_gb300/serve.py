@@ -155,9 +155,10 @@ class DepthServer:
                 r = pending.popleft()
                 w = self.cameras[r.camera]
                 waiting[(w.W, w.H, w.D)].append(r)
-            # 3. admissions: per class in arrival order, into free slots; a
-            #    request whose camera still has a frame in flight waits
-            for k in self.classes:
+            # 3. admissions: classes by the arrival of their oldest waiting
+            #    request, each in arrival order into its free slots; a request
+            #    whose camera still has a frame in flight waits
+            for k in sorted(self.classes, key=lambda c: waiting[c][0].arrival if waiting[c] else 1e30):
                 q = waiting[k]
                 while q and self.free[k] and not (sequential and self.busy):
                     pick = None
@@ -188,10 +189,12 @@ class DepthServer:
                 s.handle.close()
 
 
-def latency_stats(finished, duration):
+def latency_stats(finished, duration, cameras=None):
     lat = np.array([r.done - r.arrival for r in finished]) if finished else np.zeros(0)
+    cells = sum(cameras[r.camera].cells for r in finished) if cameras is not None else None
     return {
         "served": len(finished),
+        "served_cells_per_s": cells / duration if cells is not None and duration > 0 else None,
         "served_per_s": len(finished) / duration if duration > 0 else 0.0,
         "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
         "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
