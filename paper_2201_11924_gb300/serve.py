@@ -118,21 +118,31 @@ class DepthServer:
             slot.event.record(slot.stream)
         slot.req = req
 
-    def run(self, trace, time_limit: float | None = None, sequential: bool = False, on_done=None):
+    def run(self, trace, time_limit: float | None = None, sequential: bool = False, on_done=None,
+            policy: str = "fifo"):
         """Serve a trace in real time; returns the finished requests.
 
         time_limit: stop admitting and return after this many seconds (the
         requests still waiting are not served).  sequential: at most one
         request on the GPU at a time (the plain per-request path).
         on_done(req, depth): called when a request's depth is ready, before
-        its camera's buffers can be reused."""
+        its camera's buffers can be reused.
+        policy: "fifo" admits strictly in arrival order (a request waits
+        while an older one has no free slot, so the served mix is the
+        arrival mix); "per_class" lets each class fill its own free slots
+        (more concurrency, but under overload the classes' shares of the GPU
+        follow their slot counts, not the arrival mix)."""
         waiting = {k: collections.deque() for k in self.classes}
         busy_cams = set()
         pending = collections.deque(trace)
         finished = []
         t0 = time.perf_counter()
+        iters = 0
+        busy_sum = 0
         while pending or any(waiting.values()) or self.busy:
             now = time.perf_counter() - t0
+            iters += 1
+            busy_sum += len(self.busy)
             if time_limit is not None and now > time_limit:
                 break
             # 1. completions
@@ -158,9 +168,16 @@ class DepthServer:
             # 3. admissions: classes by the arrival of their oldest waiting
             #    request, each in arrival order into its free slots; a request
             #    whose camera still has a frame in flight waits
-            for k in sorted(self.classes, key=lambda c: waiting[c][0].arrival if waiting[c] else 1e30):
+            order = sorted(self.classes, key=lambda c: waiting[c][0].arrival if waiting[c] else 1e30)
+            for k in order:
                 q = waiting[k]
+                if policy == "fifo" and q and not self.free[k]:
+                    break                       # the oldest waiting request blocks younger ones
                 while q and self.free[k] and not (sequential and self.busy):
+                    if policy == "fifo":
+                        heads = [waiting[c][0].arrival for c in self.classes if c != k and waiting[c]]
+                        if heads and q[0].arrival > min(heads):
+                            break               # another class holds an older request
                     pick = None
                     for j in range(min(len(q), 8)):
                         if q[j].camera not in busy_cams:
@@ -180,7 +197,13 @@ class DepthServer:
                 if dt > 0:
                     time.sleep(min(dt, 0.001))
         self.torch.cuda.synchronize(self.dev)
+        # requests still on the GPU at a time-limit stop finish unrecorded
+        for s in self.busy:
+            s.req = None
+            self.free[s.cls].append(s)
+        self.busy = []
         self.backlog = sum(len(q) for q in waiting.values()) + len(pending)
+        self.stats = {"iterations": iters, "mean_busy_slots": busy_sum / max(1, iters)}
         return finished
 
     def close(self):
