@@ -82,6 +82,11 @@ __device__ __forceinline__ void lds_words(uint32_t (&w)[(NP + 1) / 2], const uin
     }
 }
 
+// keyR is padded with one word per 32: lanes whose cells map to right pixels
+// 32 apart (lanes 4 apart in a 16-lane group hold disparities 32 apart) then
+// hit different shared-memory banks.
+__device__ __forceinline__ int kr(int xr) { return xr + (xr >> 5); }
+
 // Minimum of a 32-bit value over the G lanes of a group (shuffle butterfly).
 template <int G>
 __device__ __forceinline__ uint32_t group_min(uint32_t v)
@@ -166,18 +171,22 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
 
     if (act) {
         if (interior) {
+            if constexpr (DPT == 8) {
+                *reinterpret_cast<uint4*>(sw + d0) =
+                    make_uint4(S[0] | (S[1] << 16), S[2] | (S[3] << 16), S[4] | (S[5] << 16), S[6] | (S[7] << 16));
+            } else {
 #pragma unroll
-            for (int j = 0; j < DPT; j++) {
-                sw[d0 + j] = (uint16_t)S[j];
-                atomicMin(&keyR[x - d0 - j], (S[j] << 9) | (uint32_t)(d0 + j));
+                for (int j = 0; j < DPT; j++) sw[d0 + j] = (uint16_t)S[j];
             }
+#pragma unroll
+            for (int j = 0; j < DPT; j++) atomicMin(&keyR[kr(x - d0 - j)], (S[j] << 9) | (uint32_t)(d0 + j));
         } else {
 #pragma unroll
             for (int j = 0; j < DPT; j++) {
                 const int d = d0 + j;
                 if (d < D) {
                     sw[d] = (uint16_t)S[j];
-                    if (d <= x) atomicMin(&keyR[x - d], (S[j] << 9) | (uint32_t)d);
+                    if (d <= x) atomicMin(&keyR[kr(x - d)], (S[j] << 9) | (uint32_t)d);
                 }
             }
         }
@@ -208,7 +217,7 @@ size_t select_smem(int W, int paths, int stages)
     constexpr int Dp = G * 2 * NP;
     constexpr int kPix = kSelWarps * (32 / G);
     const size_t ring = (size_t)stages * kPix * paths * Dp;
-    return ring + 8 * kMaxStages + (size_t)W * (4 + 4 + 2 + 1) + (size_t)kPix * Dp * 2 + 64;
+    return ring + 8 * kMaxStages + (size_t)(W + W / 32) * 4 + (size_t)W * (4 + 2 + 1) + (size_t)kPix * Dp * 2 + 64;
 }
 
 // Items are (pair, row); blocks are persistent over them.
@@ -225,12 +234,12 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, i
     extern __shared__ __align__(128) uint8_t smem[];
     const size_t pbytes = (size_t)paths * Dp;   // one pixel's path costs
     const size_t stage_bytes = kPix * pbytes;
-    uint8_t* ring = smem;
+    uint8_t* ring = smem;                                              // stages x stage_bytes (multiple of 256)
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * stage_bytes);
-    uint32_t* keyR = reinterpret_cast<uint32_t*>(bars + kMaxStages);   // W
-    float* dispf = reinterpret_cast<float*>(keyR + W);                 // W
-    uint16_t* sbuf = reinterpret_cast<uint16_t*>(dispf + W);           // kPix x Dp
-    int16_t* dstar = reinterpret_cast<int16_t*>(sbuf + kPix * Dp);     // W
+    uint16_t* sbuf = reinterpret_cast<uint16_t*>(bars + kMaxStages);   // kPix x Dp, 16-byte aligned
+    uint32_t* keyR = reinterpret_cast<uint32_t*>(sbuf + kPix * Dp);    // W + W/32 (padded)
+    float* dispf = reinterpret_cast<float*>(keyR + kr(W));             // W
+    int16_t* dstar = reinterpret_cast<int16_t*>(dispf + W);            // W
     uint8_t* ufail = reinterpret_cast<uint8_t*>(dstar + W);            // W
     __shared__ int abort_flag;
 
@@ -258,7 +267,7 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, i
                            rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
             }
         }
-        for (int i = threadIdx.x; i < W; i += kSelThreads) keyR[i] = 0xffffffffu;
+        for (int i = threadIdx.x; i < kr(W); i += kSelThreads) keyR[i] = 0xffffffffu;
         __syncthreads();
         for (int st = 0; st < nst; st++, seq++) {
             const int k = seq % kStages;
@@ -290,7 +299,7 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, i
                 if (xr < 0) {
                     m |= 2;
                 } else {
-                    const int dr = (int)(keyR[xr] & 511u);
+                    const int dr = (int)(keyR[kr(xr)] & 511u);
                     const int diff = ds > dr ? ds - dr : dr - ds;
                     if (diff > lr_max_diff) m |= 2;
                 }
