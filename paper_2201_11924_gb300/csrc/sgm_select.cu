@@ -344,24 +344,34 @@ cudaError_t dev_limits(DevLimits& out)
     return cudaSuccess;
 }
 
-// Raises the kernel's dynamic shared-memory limit when a launch needs more
-// than any earlier one on this device (setting it on every launch would put
-// a function-attribute call between concurrent launches of other streams).
-template <typename K>
-cudaError_t ensure_smem(K kernel, size_t bytes)
+// Raises a kernel's dynamic shared-memory limit when a launch needs more than
+// any earlier launch of that kernel on this device (setting it on every
+// launch would put a function-attribute call between concurrent launches of
+// other streams).  Entries are keyed by (device, kernel address).
+cudaError_t ensure_smem(const void* kernel, size_t bytes)
 {
-    constexpr int kMaxDev = 64;
-    static size_t set_to[kMaxDev] = {};
+    struct Entry {
+        int dev;
+        const void* fn;
+        size_t bytes;
+    };
+    constexpr int kMaxEntries = 256;
+    static Entry table[kMaxEntries];
+    static int used = 0;
     static std::mutex mu;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lock(mu);
-    if (bytes <= set_to[dev]) return cudaSuccess;
+    Entry* hit = nullptr;
+    for (int i = 0; i < used; i++)
+        if (table[i].dev == dev && table[i].fn == kernel) { hit = &table[i]; break; }
+    if (hit && bytes <= hit->bytes) return cudaSuccess;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) set_to[dev] = bytes;
-    return e;
+    if (e != cudaSuccess) return e;
+    if (hit) hit->bytes = bytes;
+    else if (used < kMaxEntries) table[used++] = Entry{dev, kernel, bytes};
+    return cudaSuccess;
 }
 
 template <int NP, int G, int N>
@@ -386,7 +396,7 @@ cudaError_t select_chunk(const Params& p, const PairPtrs* pairs, int n, const Tu
         while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > (size_t)optin) stages--;
     const size_t smem = select_smem<NP, G>(p.W, p.paths, stages);
     if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = ensure_smem(sgm_select_kernel<NP, G, N>, smem);
+    e = ensure_smem(reinterpret_cast<const void*>(sgm_select_kernel<NP, G, N>), smem);
     if (e != cudaSuccess) return e;
     const int items = n * p.H;
     const int grid = items < blocks_per_sm * nsm ? items : blocks_per_sm * nsm;   // persistent over rows
