@@ -7,7 +7,7 @@
 #include <cuda_fp16.h>
 
 template <int OP>
-__device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b)
+__device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b, uint32_t c = 0)
 {
     uint32_t d;
     if constexpr (OP == 0) asm volatile("add.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
@@ -38,6 +38,23 @@ __device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b)
     else if constexpr (OP == 25) asm volatile("min.u16x2 %0, %1, %2;\n\tprmt.b32 %0, %0, %2, 0x5432;" : "=r"(d) : "r"(a), "r"(b));
     else if constexpr (OP == 26) asm volatile("min.f16x2 %0, %1, %2;\n\tadd.rn.f16x2 %0, %0, %2;" : "=r"(d) : "r"(a), "r"(b));
     else if constexpr (OP == 27) asm volatile("min.u16x2 %0, %1, %2;\n\tmad.lo.u32 %0, %0, %2, 7;" : "=r"(d) : "r"(a), "r"(b));
+    // DPX (dynamic-programming) intrinsics: three-input min and fused add-min
+    else if constexpr (OP == 28) d = __vimin3_u16x2(a, b, c);
+    else if constexpr (OP == 29) d = __viaddmin_u16x2(a, b, c);
+    else if constexpr (OP == 30) d = __vimin3_u32(a, b, c);
+    else if constexpr (OP == 31) d = __vimin3_s16x2(a, b, c);
+    else if constexpr (OP == 32) { d = __vimin3_u16x2(a, b, c); asm volatile("min.u16x2 %0, %0, %1;" : "+r"(d) : "r"(b)); }
+    else if constexpr (OP == 33) { d = __vimin3_u16x2(a, b, c); asm volatile("prmt.b32 %0, %0, %1, 0x5432;" : "+r"(d) : "r"(b)); }
+    else if constexpr (OP == 34) { d = __vimin3_u16x2(a, b, c); asm volatile("add.u32 %0, %0, %1;" : "+r"(d) : "r"(b)); }
+    else if constexpr (OP == 36) asm volatile("and.b32 %0, %1, 0x00ff00ff;\n\txor.b32 %0, %0, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 37) asm volatile("shr.u32 %0, %1, 8;\n\txor.b32 %0, %0, %2;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 38) { d = __vimin3_u16x2(a, b, c); asm volatile("lop3.b32 %0, %0, %1, 0x00ff00ff, 0xc0;" : "+r"(d) : "r"(b)); }
+    else if constexpr (OP == 39) { d = __vimin3_u16x2(a, b, c); asm volatile("mad.lo.u32 %0, %0, 256, %1;" : "+r"(d) : "r"(b)); }
+    else if constexpr (OP == 40) { d = __vimin3_u16x2(a, b, c); asm volatile("shr.u32 %0, %0, 8;" : "+r"(d)); }
+    else if constexpr (OP == 41) asm volatile("add.u32 %0, %1, %2;\n\tsub.u32 %0, %0, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    else if constexpr (OP == 42) { d = __vimin3_u16x2(a, b, c); asm volatile("add.u32 %0, %0, %1;\n\tsub.u32 %0, %0, %2;" : "+r"(d) : "r"(b), "r"(c)); }
+    else if constexpr (OP == 43) asm volatile("prmt.b32 %0, %1, %2, 0x5432;\n\tlop3.b32 %0, %0, %2, 0x00ff00ff, 0xc0;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 35) { d = __viaddmin_u16x2(a, b, c); asm volatile("min.u16x2 %0, %0, %1;" : "+r"(d) : "r"(b)); }
     return d;
 }
 
@@ -51,7 +68,7 @@ __global__ void __launch_bounds__(1024) kern(uint32_t* out, long long* cyc, int 
     long long t0 = clock64();
     for (int it = 0; it < iters; it++) {
 #pragma unroll
-        for (int i = 0; i < 8; i++) x[i] = op<OP>(x[i], x[(i + 1) & 7]);
+        for (int i = 0; i < 8; i++) x[i] = op<OP>(x[i], x[(i + 1) & 7], x[(i + 2) & 7]);
     }
     __syncthreads();
     long long t1 = clock64();
@@ -209,6 +226,22 @@ int main()
     run<25>("min.u16x2 + prmt", nsm, out, cyc, 2);
     run<27>("min.u16x2 + mad.lo.u32", nsm, out, cyc, 2);
     run<21>("redux.sync.min", nsm, out, cyc);
+    run<28>("vimin3.u16x2", nsm, out, cyc);
+    run<29>("viaddmin.u16x2", nsm, out, cyc);
+    run<30>("vimin3.u32", nsm, out, cyc);
+    run<31>("vimin3.s16x2", nsm, out, cyc);
+    run<32>("vimin3.u16x2 + min.u16x2", nsm, out, cyc, 2);
+    run<33>("vimin3.u16x2 + prmt", nsm, out, cyc, 2);
+    run<34>("vimin3.u16x2 + add.u32", nsm, out, cyc, 2);
+    run<35>("viaddmin.u16x2 + min.u16x2", nsm, out, cyc, 2);
+    run<36>("and + xor", nsm, out, cyc, 2);
+    run<37>("shr + xor", nsm, out, cyc, 2);
+    run<38>("vimin3.u16x2 + lop3", nsm, out, cyc, 2);
+    run<39>("vimin3.u16x2 + mad.lo", nsm, out, cyc, 2);
+    run<40>("vimin3.u16x2 + shr", nsm, out, cyc, 2);
+    run<41>("add + sub (iadd3)", nsm, out, cyc, 2);
+    run<42>("vimin3.u16x2 + add + sub", nsm, out, cyc, 3);
+    run<43>("prmt + lop3", nsm, out, cyc, 2);
     lat<1>("min.u32", out, cyc);
     lat<2>("min.u16x2", out, cyc);
     lat<4>("prmt", out, cyc);
@@ -216,6 +249,8 @@ int main()
     lat<6>("shfl.bfly", out, cyc);
     lat<21>("redux.sync.min", out, cyc);
     lat<5>("popc", out, cyc);
+    lat<28>("vimin3.u16x2", out, cyc);
+    lat<29>("viaddmin.u16x2", out, cyc);
     mem_probe(nsm);
     cudaFree(out);
     cudaFree(cyc);

@@ -161,7 +161,7 @@ int simsense_compute_debug(simsense_t h, const uint8_t* left_u8, const uint8_t* 
  * library's code, held until the process exits).  It calls no cudaMalloc,
  * cudaFree or allocating library routine.
  *   - The problem must fit: 2 * round256(W*H*code bytes)
- *     + round256(W*H*Dp) + paths*W*H*Dp <= SIMSENSE_NOALLOC_SCRATCH_BYTES,
+ *     + round256(W*H*Dp) + 256 + paths*W*H*Dp <= SIMSENSE_NOALLOC_SCRATCH_BYTES,
  *     with code bytes = 4 when w*h - 1 <= 32 else 8, and Dp = 64 * ceil(D/64).  Larger problems, like
  *     any other out-of-range argument, return SIMSENSE_ERR_INVALID_ARG.
  *     (320x240, D = 64, 4 paths fits; 1280x720 does not.)
@@ -261,9 +261,10 @@ int simsense_batch_num_classes(simsense_batch_t b);
 int simsense_batch_class_info(simsense_batch_t b, int c, simsense_pair_params_t* params, int* npairs);
 
 /*
- * Launch choices of class c: prefetch = cost words in flight per scanline of
- * the path kernel (4, 8 or 12), select_blocks = selection-kernel blocks per
- * SM (1 or 2).  Results do not depend on them.
+ * Launch choices of class c: prefetch = pixels of cost in flight per
+ * scanline of the path kernel (8, 12 or 16), select_blocks = selection-kernel
+ * blocks per SM (1: one block of 1024 threads, 2: two blocks of 512 threads).
+ * Results do not depend on them.
  */
 int simsense_batch_get_tuning(simsense_batch_t b, int c, int* prefetch, int* select_blocks);
 int simsense_batch_set_tuning(simsense_batch_t b, int c, int prefetch, int select_blocks);

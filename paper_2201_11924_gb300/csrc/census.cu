@@ -26,9 +26,11 @@ census_kernel(PairTable<N> pt, int W, int H, int ww_rt, int wh_rt)
     __shared__ uint8_t tile[kTileH * kTileW];
     const int ww = WW > 0 ? WW : ww_rt;
     const int wh = WH > 0 ? WH : wh_rt;
-    const PairPtrs& pp = pt.p[blockIdx.z >> 1];
-    const uint8_t* img = (blockIdx.z & 1) ? pp.right : pp.left;
-    CodeT* out = static_cast<CodeT*>((blockIdx.z & 1) ? pp.codes_right : pp.codes_left);
+    // fields read one by one: a reference to the parameter array element would
+    // copy the table to local memory
+    const int pair = blockIdx.z >> 1;
+    const uint8_t* img = (blockIdx.z & 1) ? pt.p[pair].right : pt.p[pair].left;
+    CodeT* out = static_cast<CodeT*>((blockIdx.z & 1) ? pt.p[pair].codes_right : pt.p[pair].codes_left);
     const int rx = ww >> 1, ry = wh >> 1;
     const int tw = kTX + 2 * rx, th = kTY + 2 * ry;
     const int gx0 = blockIdx.x * kTX - rx, gy0 = blockIdx.y * kTY - ry;

@@ -35,10 +35,11 @@ cost_kernel(PairTable<N> pt, int W, int D, int nbits)
     constexpr int Dp = 32 * DPT;
     __shared__ CodeT sR[kCostPix + Dp];
     __shared__ CodeT sL[kCostPix];
-    const PairPtrs& pp = pt.p[blockIdx.z];
-    const CodeT* __restrict__ cL = static_cast<const CodeT*>(pp.codes_left);
-    const CodeT* __restrict__ cR = static_cast<const CodeT*>(pp.codes_right);
-    uint8_t* __restrict__ C = pp.cost;
+    // fields read one by one: a reference to the parameter array element would
+    // copy the table to local memory
+    const CodeT* __restrict__ cL = static_cast<const CodeT*>(pt.p[blockIdx.z].codes_left);
+    const CodeT* __restrict__ cR = static_cast<const CodeT*>(pt.p[blockIdx.z].codes_right);
+    uint8_t* __restrict__ C = pt.p[blockIdx.z].cost;
     const int y = blockIdx.y, x0 = blockIdx.x * kCostPix;
     const CodeT* rowL = cL + (size_t)y * W;
     const CodeT* rowR = cR + (size_t)y * W;

@@ -36,6 +36,7 @@ struct Scratch {
     uint8_t* cost = nullptr;       // H x W x Dp uint8, Hamming cost C
     uint8_t* paths = nullptr;      // H x W x paths x Dp uint8, L_r per path
     int* status = nullptr;         // device status word (SIMSENSE_ERR_TIMEOUT after a bounded wait gave up)
+    uint32_t* work = nullptr;      // work counter of the path kernel (zeroed before each launch)
     uint8_t* stage_left = nullptr; // host-call staging: H x W uint8
     uint8_t* stage_right = nullptr;
     float* stage_depth = nullptr;  // H x W float32
@@ -52,6 +53,8 @@ struct PairPtrs {
     uint8_t* cost;           // H x W x Dp
     uint8_t* vol;            // H x W x paths x Dp
     float* depth;            // H x W
+    uint32_t* work;          // 4-byte work counter of the path kernel; a launch over
+                             // several pairs uses the first pair's
 };
 
 // Pairs of one launch, passed by value as a kernel parameter (nothing to
@@ -66,9 +69,13 @@ struct PairTable {
 // Launch choices the autotuner may change (defaults are the measured best
 // for 1280x720, D = 128 on GB300).
 struct Tuning {
-    int prefetch = 8;        // path kernel: cost words in flight per scanline (4, 8 or 12)
-    int select_blocks = 2;   // selection kernel: blocks per SM (1 or 2)
+    int prefetch = 16;       // path kernel: pixels of cost in flight per scanline (8, 12 or 16)
+    int select_blocks = 1;   // selection kernel: 1 = one 1024-thread block per SM, 2 = two 512-thread blocks
 };
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` when a launch needs
+// more than any earlier launch of that kernel on the current device.
+cudaError_t ensure_smem(const void* kernel, size_t bytes);
 
 // Optional outputs of the selection kernel (device pointers, may be null).
 struct SelectDebug {

@@ -3,29 +3,40 @@
 // warp-based optimization").
 //
 // Every path direction r splits the image into independent scanlines (rows,
-// columns or diagonals).  A group of G lanes walks one scanline (G = 8, 16 or
-// 32 so that a lane holds 8 disparities, or 6 when Dp = 192; a warp walks
-// 32 / G scanlines side by side); lane l of a group holds the disparities
-// l*DPT .. l*DPT + DPT - 1 of the padded range Dp as DPT/2 packed 16-bit
-// pairs.  At each pixel p the group
-//   1. takes C(p, .) from the byte cost volume (loaded 8 steps ahead, so the
-//      load latency overlaps the recurrence);
-//   2. evaluates  L(p,d) = C(p,d) + min(L'(d), L'(d-1)+P1, L'(d+1)+P1, m'+P2) - m'
-//      on the pairs: min(L'(d-1), L'(d+1)) of both cells of a pair is one
-//      min.u16x2 of the pair shifted down and up by one cell (byte permutes
-//      of neighbouring pairs, plus one shuffle from each neighbouring lane for
-//      the cells beyond the lane's range), then +P1, min with L'(d), min with
-//      m'+P2, and one 3-input add of C - m';
-//   3. stores L(p, .) as bytes (L <= nbits + P2 <= 255) into the path volume,
-//      layout [y][x][r][Dp] so that the selection kernel reads one pixel's
-//      paths contiguously;
-//   4. forms m = min_d L(p, d): a min.u16x2 over the lane's pairs, then a
-//      shuffle butterfly over the group.
-// The scanlines of a warp may differ in length (diagonals); the warp runs to
-// the longest and the lanes of a finished scanline stop loading and storing.
-// Padded disparities carry cost 255 in the cost volume (see cost.cu).  The
-// cells d = -1 and d = Dp beyond the first and last lane read 0x3FFF, larger
-// than any m' + P2, which is the recurrence's +infinity.
+// columns or diagonals).  A group of G lanes walks one scanline (a warp walks
+// 32 / G scanlines side by side); lane l of a group holds 4*NQ consecutive
+// disparities of the padded range Dp, as NQ quads.  A quad's four cells
+// d0..d3 live in two packed 16-bit pairs, E = (d0, d2) and O = (d1, d3), so
+// that the neighbours d - 1 and d + 1 of one pair are mostly the other pair
+// of the quad (only one byte permute per pair is needed for the rest).
+//
+// The recurrence L(p,d) = C(p,d) + min(L'(d), L'(d-1)+P1, L'(d+1)+P1, m'+P2) - m'
+// is evaluated with a three-input minimum (a DPX instruction on this GPU):
+// the lane keeps, besides L' + P1, the clamped value min(L'(d), m' + P2), and
+//   min(L'(d), m'+P2, L'(d-1)+P1, L'(d+1)+P1)
+//     = min3(min(L'(d), m'+P2), L'(d-1)+P1, L'(d+1)+P1).
+// Per pixel the group
+//   1. takes C(p, .) from the byte cost volume and splits each word into its
+//      even and odd cells.  The cost is copied PF pixels ahead into a ring
+//      in shared memory with cp.async, so the DRAM latency overlaps PF steps
+//      of the recurrence without holding the ring in registers;
+//   2. evaluates the recurrence on the pairs (one shuffle from each
+//      neighbouring lane supplies the cells beyond the lane's range);
+//   3. stores L(p, .) as bytes (L <= nbits + P2 <= 255 for every real
+//      disparity) into the path volume, layout [y][x][r][Dp], so that the
+//      selection kernel reads one pixel's paths contiguously;
+//   4. forms m = min_d L(p, d): a three-input-min tree over the lane's pairs,
+//      then a reduction over the group (redux.sync for a whole warp, a
+//      shuffle butterfly otherwise).
+// All values stay below 2^15, so 32-bit adds of packed pairs never carry
+// across the halves.  Padded disparities carry cost 255, which keeps their L
+// at 255 or more: they never undercut a real candidate and never lower m.
+//
+// Scheduling: a warp takes one work item (a group of scanlines of one
+// direction of one pair), numbered longest scanlines first: the longer of the
+// horizontal and vertical directions, then the other, then the diagonals
+// ranked by length.  The longest scanlines bound the kernel's duration, so
+// they start first, and the short ones fill the SMs at the end.
 #include "internal.h"
 #include "simd.cuh"
 
@@ -36,8 +47,7 @@ constexpr int kPathThreads = 256;
 constexpr uint32_t kInfPair = 0x3fff3fffu;
 
 // Path directions: the value at p comes from p - r.  The first four are the
-// 4-path set (horizontal and vertical), the last four the diagonals.  The
-// horizontal ones come first so that their long scanlines start first.
+// 4-path set (horizontal and vertical), the last four the diagonals.
 __device__ __forceinline__ void path_dir(int r, int& rx, int& ry)
 {
     switch (r) {
@@ -54,7 +64,8 @@ __device__ __forceinline__ void path_dir(int r, int& rx, int& ry)
 
 // Entry pixel of scanline `scan` of direction (rx, ry) and the number of
 // pixels on it (0 if there is no such scanline).  Entry pixels are those whose
-// predecessor p - r lies outside the image.
+// predecessor p - r lies outside the image.  Diagonal scanlines 0 .. W-1 enter
+// on the first row the path meets (x = scan), W .. W+H-2 on the first column.
 __device__ __forceinline__ int scan_start(int scan, int rx, int ry, int W, int H, int& x, int& y)
 {
     if (ry == 0) {
@@ -70,10 +81,10 @@ __device__ __forceinline__ int scan_start(int scan, int rx, int ry, int W, int H
         return H;
     }
     if (scan >= W + H - 1) return 0;
-    if (scan < W) {                   // entries on the first row the path meets
+    if (scan < W) {
         x = scan;
         y = ry > 0 ? 0 : H - 1;
-    } else {                          // entries on the first column, other rows
+    } else {
         const int k = scan - W + 1;
         x = rx > 0 ? 0 : W - 1;
         y = ry > 0 ? k : H - 1 - k;
@@ -83,84 +94,105 @@ __device__ __forceinline__ int scan_start(int scan, int rx, int ry, int W, int H
     return nx < ny ? nx : ny;
 }
 
-// Raw bytes of NP pairs (2*NP consecutive bytes; 8-byte aligned for NP = 4,
-// 4-byte for NP = 2, 2-byte otherwise).
-template <int NP>
-struct Raw { uint32_t w[(NP + 1) / 2]; };
-
-__device__ __forceinline__ uint64_t keep_policy()
+// Diagonal scanline of rank j (0 <= j < W + H - 1) in order of non-increasing
+// length.  With m = min(W, H), M = max(W, H): M - m + 1 scanlines have length
+// m, then every length l = m-1 .. 1 occurs twice, once entering on the first
+// row (u = W - l steps from the path's starting corner) and once on the first
+// column (k = H - l rows from it).
+__device__ __forceinline__ int diag_scan(int j, int rx, int W, int H)
 {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
+    const int m = W < H ? W : H;
+    const int M = W < H ? H : W;
+    const int full = M - m + 1;
+    int u = -1, k = 0;
+    if (j < full) {
+        if (W >= H) u = j;
+        else if (j == 0) u = 0;
+        else k = j;
+    } else {
+        const int t = j - full;
+        const int l = m - 1 - (t >> 1);
+        if ((t & 1) == 0) u = W - l;
+        else k = H - l;
+    }
+    if (u >= 0) return rx > 0 ? u : W - 1 - u;
+    return W - 1 + k;
 }
 
-// Loads the 2*NP cost bytes at p into r when pred holds, else leaves r as it
-// is.  The predicate sits inside the asm and r is a read-write operand, so
-// the load writes the ring registers directly and nothing waits for it until
-// the ring slot is unpacked PF steps later (a load into a temporary followed
-// by a conditional move would wait for the data at once).
-template <int NP>
-__device__ __forceinline__ void load_raw(Raw<NP>& r, const uint8_t* p, uint64_t pol, bool pred)
+// Asynchronous copy of the lane's 4*NQ cost bytes into its shared-memory ring
+// slot (skipped when pred is false), then a commit: every step commits one
+// group, so "the copy of pixel i has landed" is "at most PF - 1 groups are
+// still pending" (cp.async.wait_group PF - 1).
+template <int NQ>
+__device__ __forceinline__ void cp_cost(uint32_t dst, const uint8_t* src, bool pred)
 {
-    if constexpr (NP == 1) {
-        asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 h;\n\tsetp.ne.b32 q, %2, 0;\n\t"
-                     "@q ld.global.nc.L2::cache_hint.b16 h, [%1], %3;\n\t"
-                     "@q cvt.u32.u16 %0, h;\n\t}"
-                     : "+r"(r.w[0]) : "l"(p), "r"((int)pred), "l"(pol));
-    } else if constexpr (NP == 2) {
-        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
-                     "@q ld.global.nc.L2::cache_hint.b32 %0, [%1], %3;\n\t}"
-                     : "+r"(r.w[0]) : "l"(p), "r"((int)pred), "l"(pol));
-    } else if constexpr (NP == 3) {
-        asm volatile("{\n\t.reg .pred q;\n\t.reg .b16 a, b, c;\n\tsetp.ne.b32 q, %3, 0;\n\t"
-                     "@q ld.global.nc.L2::cache_hint.b16 a, [%2], %4;\n\t"
-                     "@q ld.global.nc.L2::cache_hint.b16 b, [%2+2], %4;\n\t"
-                     "@q ld.global.nc.L2::cache_hint.b16 c, [%2+4], %4;\n\t"
-                     "@q mov.b32 %0, {a, b};\n\t"
-                     "@q cvt.u32.u16 %1, c;\n\t}"
-                     : "+r"(r.w[0]), "+r"(r.w[1]) : "l"(p), "r"((int)pred), "l"(pol));
+    if (pred) {
+        if constexpr (NQ == 1) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(src) : "memory");
+        } else if constexpr (NQ == 2) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" :: "r"(dst), "l"(src) : "memory");
+        } else if constexpr (NQ == 3) {
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst), "l"(src) : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst + 4), "l"(src + 4) : "memory");
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(dst + 8), "l"(src + 8) : "memory");
+        } else {
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(dst), "l"(src) : "memory");
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+template <int NQ>
+__device__ __forceinline__ void lds_cost(uint32_t (&w)[NQ], uint32_t a)
+{
+    if constexpr (NQ == 1) {
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w[0]) : "r"(a) : "memory");
+    } else if constexpr (NQ == 2) {
+        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "r"(a) : "memory");
+    } else if constexpr (NQ == 3) {
+        asm volatile("ld.shared.b32 %0, [%3];\n\tld.shared.b32 %1, [%3+4];\n\tld.shared.b32 %2, [%3+8];"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]) : "r"(a) : "memory");
     } else {
-        asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t"
-                     "@q ld.global.nc.L2::cache_hint.v2.b32 {%0, %1}, [%2], %4;\n\t}"
-                     : "+r"(r.w[0]), "+r"(r.w[1]) : "l"(p), "r"((int)pred), "l"(pol));
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(a) : "memory");
     }
 }
 
-template <int NP>
-__device__ __forceinline__ void unpack(const Raw<NP>& r, uint32_t (&c)[NP])
+template <int NQ>
+__device__ __forceinline__ void store_words(uint8_t* p, const uint32_t (&w)[NQ])
 {
-#pragma unroll
-    for (int k = 0; k < NP; k++) c[k] = (k & 1) ? hi_bytes(r.w[k >> 1]) : lo_bytes(r.w[k >> 1]);
-}
-
-template <int NP>
-__device__ __forceinline__ void store_pairs(uint8_t* p, const uint32_t (&L)[NP])
-{
-    if constexpr (NP == 1) {
-        __stcs(reinterpret_cast<unsigned short*>(p), (unsigned short)__byte_perm(L[0], 0, 0x0020));
-    } else if constexpr (NP == 2) {
-        __stcs(reinterpret_cast<unsigned int*>(p), pack_bytes(L[0], L[1]));
-    } else if constexpr (NP == 3) {
-        unsigned short* q = reinterpret_cast<unsigned short*>(p);
-        __stcs(q, (unsigned short)__byte_perm(L[0], 0, 0x0020));
-        __stcs(q + 1, (unsigned short)__byte_perm(L[1], 0, 0x0020));
-        __stcs(q + 2, (unsigned short)__byte_perm(L[2], 0, 0x0020));
+    if constexpr (NQ == 1) {
+        __stcs(reinterpret_cast<unsigned int*>(p), w[0]);
+    } else if constexpr (NQ == 2) {
+        __stcs(reinterpret_cast<uint2*>(p), make_uint2(w[0], w[1]));
+    } else if constexpr (NQ == 3) {
+        unsigned int* q = reinterpret_cast<unsigned int*>(p);
+        __stcs(q, w[0]);
+        __stcs(q + 1, w[1]);
+        __stcs(q + 2, w[2]);
     } else {
-        __stcs(reinterpret_cast<uint2*>(p), make_uint2(pack_bytes(L[0], L[1]), pack_bytes(L[2], L[3])));
+        __stcs(reinterpret_cast<uint4*>(p), make_uint4(w[0], w[1], w[2], w[3]));
     }
 }
 
-// (m, m) with m the minimum over the group's cells: the lane minimum is
-// duplicated into both halves, then reduced over the group: one redux.sync
-// for a whole warp, a shuffle butterfly for a partial-warp group (measured
-// faster here than redux.sync with a partial mask).
-template <int NP, int G>
-__device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NP])
+// (m, m) with m the minimum over the group's cells: a three-input-min tree
+// over the lane's 2*NQ pairs, the two halves, then the group (one redux.sync
+// for a whole warp, a shuffle butterfly for a partial-warp group).
+template <int NQ, int G>
+__device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[2 * NQ])
 {
-    uint32_t mn = L[0];
-#pragma unroll
-    for (int k = 1; k < NP; k++) mn = vmin2(mn, L[k]);
+    uint32_t mn;
+    if constexpr (NQ == 1) {
+        mn = vmin2(L[0], L[1]);
+    } else if constexpr (NQ == 2) {
+        mn = vmin2(vmin3(L[0], L[1], L[2]), L[3]);
+    } else if constexpr (NQ == 3) {
+        mn = vmin3(vmin3(L[0], L[1], L[2]), L[3], vmin3(L[4], L[5], L[5]));
+    } else {
+        mn = vmin3(vmin3(L[0], L[1], L[2]), vmin3(L[3], L[4], L[5]), vmin2(L[6], L[7]));
+    }
     mn = vmin2(mn, __byte_perm(mn, 0, 0x1032));
     if constexpr (G == 32) {
         return __reduce_min_sync(0xffffffffu, mn);
@@ -171,132 +203,225 @@ __device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[NP])
     }
 }
 
-// G lanes walk one scanline (32 / G scanlines per warp), each holding NP pairs.
-// The cost of the next PF pixels is kept in flight in a register ring (slot
-// i % PF, a static index inside the PF-times unrolled loop), which hides the
-// DRAM latency behind PF steps of the recurrence.
-template <int NP, int G, int PF>
-__device__ __forceinline__ void walk(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, int paths,
-                                     uint8_t* __restrict__ vol, int r, int rx, int ry)
+// Steps base .. base + PF - 1 of a walk (fewer if the walk ends first).
+// Guard = false: every lane's pixel i and prefetch target i + PF lie on its
+// scanline, so loads and stores need no predicate; Guard = true: lanes whose
+// scanline is shorter than the warp's longest stop loading and storing.
+template <int NQ, int G, int PF, bool Guard>
+__device__ __forceinline__ void walk_steps(int base, int n, int len, uint32_t ring, const uint8_t*& cf,
+                                           long long cstep, uint8_t*& op, long long ostep,
+                                           uint32_t (&Lc)[2 * NQ], uint32_t (&Lp)[2 * NQ], uint32_t& mm,
+                                           uint32_t p1, uint32_t p2, uint32_t edge_lo, uint32_t edge_hi,
+                                           uint32_t hi8)
 {
-    constexpr int DPT = 2 * NP;
+#pragma unroll
+    for (int k = 0; k < PF; k++) {
+        const int i = base + k;
+        if (Guard && i >= n) break;            // uniform
+        uint32_t cw[NQ];
+        cp_wait<PF - 1>();                     // the copy of pixel i has landed
+        lds_cost<NQ>(cw, ring + k * 512);
+        // O pair of the quad below the lane's range, E pair above it
+        const uint32_t o_below = __shfl_up_sync(0xffffffffu, Lp[2 * NQ - 1], 1, G) + edge_lo;
+        const uint32_t e_above = __shfl_down_sync(0xffffffffu, Lp[0], 1, G) + edge_hi;
+        uint32_t L[2 * NQ], out[NQ];
+#pragma unroll
+        for (int q = 0; q < NQ; q++) {
+            const uint32_t Oprev = q == 0 ? o_below : Lp[2 * q - 1];
+            const uint32_t Enext = q == NQ - 1 ? e_above : Lp[2 * q + 2];
+            // E = (d0, d2): d + 1 is O = (d1, d3), d - 1 is (d-1, d1)
+            const uint32_t tE = vmin3(Lc[2 * q], Lp[2 * q + 1], shift_pair(Oprev, Lp[2 * q + 1]));
+            // O = (d1, d3): d - 1 is E = (d0, d2), d + 1 is (d2, d4)
+            const uint32_t tO = vmin3(Lc[2 * q + 1], Lp[2 * q], shift_pair(Lp[2 * q], Enext));
+            // cost bytes (c0, c1, c2, c3) -> (c0, c2) and (c1, c3)
+            const uint32_t cE = cw[q] & 0x00ff00ffu;
+            const uint32_t cO = __umulhi(cw[q] - cE, hi8);     // (cw - cE) >> 8
+            L[2 * q] = tE + cE - mm;           // no borrow: every half of t is >= m'
+            L[2 * q + 1] = tO + cO - mm;
+            out[q] = L[2 * q + 1] * 256u + L[2 * q];            // bytes (L0, L1, L2, L3)
+        }
+        if (!Guard || i < len) store_words<NQ>(op, out);
+        op += ostep;
+        // slot k is free again (its bytes were read above): pixel i + PF
+        cp_cost<NQ>(ring + k * 512, cf, Guard ? i + PF < len : true);
+        cf += cstep;
+        mm = group_min<NQ, G>(L);
+        const uint32_t cap = mm + p2;
+#pragma unroll
+        for (int k2 = 0; k2 < 2 * NQ; k2++) {
+            Lc[k2] = vmin2(L[k2], cap);
+            Lp[k2] = L[k2] + p1;
+        }
+    }
+}
+
+// Walks scanline `scan` of direction r with G lanes per scanline and NQ quads
+// per lane.  The cost of the next PF pixels is in flight into the warp's
+// shared-memory ring: slot k (a static index inside the PF-times unrolled
+// loop) holds 16 bytes per lane, so the warp's ring is PF x 512 bytes.
+template <int NQ, int G, int PF>
+__device__ __forceinline__ void walk(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, int paths,
+                                     uint8_t* __restrict__ vol, int r, int rx, int ry, int scan, uint32_t hi8)
+{
+    constexpr int DPT = 4 * NQ;
     constexpr int Dp = G * DPT;
     constexpr int SPW = 32 / G;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G;
-    const int scan = (blockIdx.x * (kPathThreads / 32) + (threadIdx.x >> 5)) * SPW + lane / G;
     int x = 0, y = 0;
     const int len = scan_start(scan, rx, ry, W, H, x, y);
     const int n = SPW > 1 ? (int)__reduce_max_sync(0xffffffffu, (unsigned)len) : len;
     if (n == 0) return;                       // uniform across the warp
+    const int nmin = SPW > 1 ? (int)__reduce_min_sync(0xffffffffu, (unsigned)len) : len;
 
     const uint32_t p1 = (uint32_t)P1 * 0x10001u;
     const uint32_t p2 = (uint32_t)P2 * 0x10001u;
+    // the shuffled-in neighbour cells beyond the first and last lane become
+    // larger than any candidate (adding to the lane's own value keeps every
+    // half below 2^15)
+    const uint32_t edge_lo = gl == 0 ? kInfPair : 0u;
+    const uint32_t edge_hi = gl == G - 1 ? kInfPair : 0u;
     const long long pix0 = (long long)y * W + x;
     const long long step = (long long)ry * W + rx;      // pixel index increment along the path
     const long long cstep = step * Dp;
     const long long ostep = step * paths * Dp;
     const uint8_t* cf = C + pix0 * Dp + gl * DPT;        // cost of the next pixel to fetch
     uint8_t* op = vol + (pix0 * paths + r) * Dp + gl * DPT;
-    const uint64_t pol = keep_policy();
 
-    Raw<NP> ring[PF] = {};
+    extern __shared__ __align__(16) uint8_t path_smem[];
+    const uint32_t ring = (uint32_t)__cvta_generic_to_shared(path_smem) + (threadIdx.x >> 5) * PF * 512 + lane * 16;
 #pragma unroll
     for (int k = 0; k < PF; k++) {
-        load_raw<NP>(ring[k], cf, pol, k < len);
+        cp_cost<NQ>(ring + k * 512, cf, k < len);
         cf += cstep;
     }
-    // L' = 0 and m' = 0 before the entry pixel make the recurrence return
-    // exactly C there, which is the path's start condition.
-    uint32_t Lp[NP];
+    // State before the entry pixel: L' = 0 and m' = 0, which makes the
+    // recurrence return exactly C there (the path's start condition).
+    // Lc = min(L', m' + P2) and Lp = L' + P1 per pair, E pairs at even and O
+    // pairs at odd indices.
+    uint32_t Lc[2 * NQ], Lp[2 * NQ];
 #pragma unroll
-    for (int k = 0; k < NP; k++) Lp[k] = 0;
-    uint32_t mm = 0, cap = p2;
+    for (int k = 0; k < 2 * NQ; k++) {
+        Lc[k] = 0;
+        Lp[k] = p1;
+    }
+    uint32_t mm = 0;
 
-    for (int base = 0; base < n; base += PF) {
-#pragma unroll
-        for (int k = 0; k < PF; k++) {
-            const int i = base + k;
-            if (i >= n) break;                 // uniform
-            uint32_t Cp[NP];
-            unpack<NP>(ring[k], Cp);
-            load_raw<NP>(ring[k], cf, pol, i + PF < len);
-            cf += cstep;
-            uint32_t lo = __shfl_up_sync(0xffffffffu, Lp[NP - 1], 1, G);
-            uint32_t hi = __shfl_down_sync(0xffffffffu, Lp[0], 1, G);
-            if (gl == 0) lo = kInfPair;
-            if (gl == G - 1) hi = kInfPair;
-            uint32_t S[NP + 1];
-            S[0] = shift_pair(lo, Lp[0]);
-#pragma unroll
-            for (int q = 1; q < NP; q++) S[q] = shift_pair(Lp[q - 1], Lp[q]);
-            S[NP] = shift_pair(Lp[NP - 1], hi);
-#pragma unroll
-            for (int q = 0; q < NP; q++) {
-                uint32_t t = vmin2(S[q], S[q + 1]) + p1;
-                t = vmin2(vmin2(t, Lp[q]), cap);
-                Lp[q] = t + Cp[q] - mm;      // no borrow: every half of t is >= m'
-            }
-            if (i < len) store_pairs<NP>(op, Lp);
-            op += ostep;
-            mm = group_min<NP, G>(Lp);
-            cap = mm + p2;
-        }
+    // steps whose pixel and prefetch target lie on every lane's scanline
+    const int nmain = nmin > PF ? (nmin - PF) / PF * PF : 0;
+    int base = 0;
+    for (; base < nmain; base += PF)
+        walk_steps<NQ, G, PF, false>(base, n, len, ring, cf, cstep, op, ostep, Lc, Lp, mm, p1, p2,
+                                     edge_lo, edge_hi, hi8);
+    for (; base < n; base += PF)
+        walk_steps<NQ, G, PF, true>(base, n, len, ring, cf, cstep, op, ostep, Lc, Lp, mm, p1, p2,
+                                    edge_lo, edge_hi, hi8);
+}
+
+// Work items of one launch: warp-sized groups of scanlines, longest first.
+struct Items {
+    int nh, nv, nd;          // groups per direction: horizontal, vertical, diagonal
+    int cls_h, cls_v, cls_d; // items per class (all directions and pairs)
+    int total;
+    bool h_first;
+};
+
+__host__ __device__ inline Items make_items(int W, int H, int paths, int npairs, int spw, int spwh)
+{
+    Items it;
+    it.nh = (H + spwh - 1) / spwh;
+    it.nv = (W + spw - 1) / spw;
+    it.nd = (W + H - 1 + spw - 1) / spw;
+    it.cls_h = 2 * npairs * it.nh;
+    it.cls_v = 2 * npairs * it.nv;
+    it.cls_d = paths == 8 ? 4 * npairs * it.nd : 0;
+    it.total = it.cls_h + it.cls_v + it.cls_d;
+    it.h_first = W >= H;
+    return it;
+}
+
+// Horizontal scanlines (rows) use NQH quads per lane and GH lanes per row,
+// the other directions NQ and G (per disparity range, the layouts measured
+// fastest on GB300: wider lanes mean fewer instructions per cell but more
+// registers per thread).
+//
+// One warp per work item, item = blockIdx.x * warps + warp.  Items are
+// numbered longest first, and blocks start in index order as earlier ones
+// finish, so the long scanlines start at once and the short ones fill the
+// SMs at the end.
+template <int NQ, int G, int NQH, int GH, int PF, int N>
+__global__ void __launch_bounds__(kPathThreads)
+sgm_paths_kernel(PairTable<N> pt, int npairs, int W, int H, int P1, int P2, int paths, uint32_t hi8)
+{
+    static_assert(G * 4 * NQ == GH * 4 * NQH, "both layouts cover the same padded range");
+    constexpr int SPW = 32 / G, SPWH = 32 / GH;
+    const int lane = threadIdx.x & 31;
+    const Items it = make_items(W, H, paths, npairs, SPW, SPWH);
+    int i = blockIdx.x * (kPathThreads / 32) + (threadIdx.x >> 5);
+    if (i >= it.total) return;
+    int cls;                                   // 0 horizontal, 1 vertical, 2 diagonal
+    const int first = it.h_first ? it.cls_h : it.cls_v;
+    if (i < first) {
+        cls = it.h_first ? 0 : 1;
+    } else if (i < it.cls_h + it.cls_v) {
+        cls = it.h_first ? 1 : 0;
+        i -= first;
+    } else {
+        cls = 2;
+        i -= it.cls_h + it.cls_v;
+    }
+    const int ndir = cls == 2 ? 4 : 2;
+    const int g = i / (ndir * npairs);         // group-major: every direction and pair advances together
+    const int rem = i % (ndir * npairs);
+    const int r = (cls == 0 ? 0 : cls == 1 ? 2 : 4) + rem % ndir;
+    const int pair = rem / ndir;
+    const uint8_t* __restrict__ C = pt.p[pair].cost;
+    uint8_t* __restrict__ vol = pt.p[pair].vol;
+    int rx, ry;
+    path_dir(r, rx, ry);
+    if (cls == 0) {
+        walk<NQH, GH, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry, g * SPWH + lane / GH, hi8);
+    } else {
+        const int j = g * SPW + lane / G;
+        const int scan = cls == 1 ? j : (j < W + H - 1 ? diag_scan(j, rx, W, H) : W + H - 1);
+        walk<NQ, G, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry, scan, hi8);
     }
 }
 
-// The horizontal directions have the longest scanlines (W steps of a
-// recurrence that is inherently sequential), so they decide the kernel's
-// critical path: they are walked by whole warps (NPH pairs per lane, group
-// minimum by one redux.sync, the shortest step latency measured).  The other
-// directions are throughput-bound and use G-lane groups with NP pairs.
-template <int NP, int G, int NPH, int PF, int N>
-__global__ void __launch_bounds__(kPathThreads)
-sgm_paths_kernel(PairTable<N> pt, int W, int H, int P1, int P2, int paths)
-{
-    static_assert(G * 2 * NP == 32 * 2 * NPH, "both layouts cover the same padded range");
-    const uint8_t* __restrict__ C = pt.p[blockIdx.z].cost;      // blockIdx.z = pair
-    uint8_t* __restrict__ vol = pt.p[blockIdx.z].vol;
-    const int r = blockIdx.y;
-    int rx, ry;
-    path_dir(r, rx, ry);
-    if (ry == 0) walk<NPH, 32, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry);
-    else walk<NP, G, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry);
-}
-
-template <int NP, int G, int NPH, int PF, int N>
+template <int NQ, int G, int NQH, int GH, int PF, int N>
 cudaError_t paths_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
 {
     PairTable<N> pt{};
     for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
-    // blocks: enough for the non-horizontal directions (W + H - 1 scanlines at
-    // most, 32/G per warp) and for the horizontal ones (H scanlines, 1 per warp)
-    const int per_block = (kPathThreads / 32) * (32 / G);
-    const int nb = (p.W + p.H - 1 + per_block - 1) / per_block;
-    const int nbh = (p.H + kPathThreads / 32 - 1) / (kPathThreads / 32);
-    dim3 grid(nb > nbh ? nb : nbh, p.paths, n);
-    sgm_paths_kernel<NP, G, NPH, PF, N><<<grid, kPathThreads, 0, s>>>(pt, p.W, p.H, p.P1, p.P2, p.paths);
+    const Items it = make_items(p.W, p.H, p.paths, n, 32 / G, 32 / GH);
+    const int warps = kPathThreads / 32;
+    const int blocks = (it.total + warps - 1) / warps;
+    const size_t smem = (size_t)warps * PF * 512;
+    auto kernel = sgm_paths_kernel<NQ, G, NQH, GH, PF, N>;
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<blocks, kPathThreads, smem, s>>>(pt, n, p.W, p.H, p.P1, p.P2, p.paths, 1u << 24);
     return cudaGetLastError();
 }
 
-template <int NP, int G, int NPH, int N>
+template <int NQ, int G, int NQH, int GH, int N>
 cudaError_t paths_pf(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s)
 {
     switch (t.prefetch) {
-        case 4: return paths_chunk<NP, G, NPH, 4, N>(p, pairs, n, s);
-        case 12: return paths_chunk<NP, G, NPH, 12, N>(p, pairs, n, s);
-        default: return paths_chunk<NP, G, NPH, 8, N>(p, pairs, n, s);
+        case 8: return paths_chunk<NQ, G, NQH, GH, 8, N>(p, pairs, n, s);
+        case 16: return paths_chunk<NQ, G, NQH, GH, 16, N>(p, pairs, n, s);
+        default: return paths_chunk<NQ, G, NQH, GH, 12, N>(p, pairs, n, s);
     }
 }
 
 template <int N>
 cudaError_t paths_dp(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s)
 {
-    switch (p.Dp) {                            // lanes per scanline x 8 (or 6) disparities per lane
-        case 64: return paths_pf<4, 8, 1, N>(p, pairs, n, t, s);
-        case 128: return paths_pf<4, 16, 2, N>(p, pairs, n, t, s);
-        case 192: return paths_pf<3, 32, 3, N>(p, pairs, n, t, s);
-        case 256: return paths_pf<4, 32, 4, N>(p, pairs, n, t, s);
+    switch (p.Dp) {                            // (quads per lane, lanes per scanline): other, horizontal
+        case 64: return paths_pf<4, 4, 2, 8, N>(p, pairs, n, t, s);
+        case 128: return paths_pf<4, 8, 2, 16, N>(p, pairs, n, t, s);
+        case 192: return paths_pf<3, 16, 3, 16, N>(p, pairs, n, t, s);
+        case 256: return paths_pf<4, 16, 2, 32, N>(p, pairs, n, t, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -29,8 +29,6 @@
 namespace simsense {
 namespace {
 
-constexpr int kSelThreads = 512;
-constexpr int kSelWarps = kSelThreads / 32;
 constexpr int kMaxStages = 4;                // ring depth when shared memory allows
 constexpr uint32_t kMaxPolls = 1u << 22;     // bound on polls of one stage barrier
 
@@ -96,13 +94,21 @@ __device__ __forceinline__ uint32_t group_min(uint32_t v)
     return v;
 }
 
+__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
 // One pixel of the row for one lane group: sum, winner, uniqueness, offers to
 // the right view, parabola.  src is the pixel's first path in the stage.
-template <int NP, int G>
+// DFULL: D equals the padded range, so every cell is a real disparity.
+template <int NP, int G, int PATHS, bool DFULL>
 __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act, int y, int W, int D,
-                                             int paths, int uniq, uint32_t umagic, int subpixel, int gl,
-                                             uint16_t* sw, uint32_t* keyR, float* dispf, int16_t* dstar,
-                                             uint8_t* ufail, const SelectDebug& dbg)
+                                             int uniq, uint32_t umagic, int subpixel, int gl,
+                                             uint16_t* sw, uint32_t* keyR, uint32_t* info, uint32_t* fit,
+                                             const SelectDebug& dbg)
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
@@ -113,41 +119,37 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
     const int chunk = G == 16 ? (gl + 8 * ((threadIdx.x & 31) / 16)) % 16 : gl;
     const int d0 = chunk * DPT;
     const size_t pix = (size_t)y * W + x;
-    // path sums: even[k] holds cells (4k, 4k+2), odd[k] cells (4k+1, 4k+3)
-    uint32_t even[NW], odd[NW];
+    // path sums: ev[k] holds cells (4k, 4k+2), od[k] cells (4k+1, 4k+3) as
+    // 16-bit pairs (8 bytes of at most 255 cannot carry out of a half); two
+    // paths per three-input add
+    uint32_t ev[NW], od[NW];
 #pragma unroll
-    for (int k = 0; k < NW; k++) { even[k] = 0; odd[k] = 0; }
+    for (int k = 0; k < NW; k++) { ev[k] = 0; od[k] = 0; }
 #pragma unroll
-    for (int r = 0; r < 8; r++) {
-        if (r < paths) {
-            uint32_t w[NW];
-            lds_words<NP>(w, src + r * Dp + d0);
+    for (int r = 0; r < PATHS; r += 2) {
+        uint32_t a[NW], b[NW];
+        lds_words<NP>(a, src + r * Dp + d0);
+        lds_words<NP>(b, src + (r + 1) * Dp + d0);
 #pragma unroll
-            for (int k = 0; k < NW; k++) {
-                even[k] += w[k] & 0x00ff00ffu;
-                odd[k] += (w[k] >> 8) & 0x00ff00ffu;
-            }
+        for (int k = 0; k < NW; k++) {
+            ev[k] += (a[k] & 0x00ff00ffu) + (b[k] & 0x00ff00ffu);
+            od[k] += __byte_perm(a[k], 0, 0x4341) + __byte_perm(b[k], 0, 0x4341);
         }
     }
-    // cell j of the lane (d = d0 + j): word j/4, byte j%4
+    // cell j of the lane (d = d0 + j): word j/4, parity j%2, half (j/2)%2
     uint32_t S[DPT];
 #pragma unroll
     for (int j = 0; j < DPT; j++) {
-        const uint32_t w = (j & 1) ? odd[j >> 2] : even[j >> 2];
+        const uint32_t w = (j & 1) ? od[j >> 2] : ev[j >> 2];
         S[j] = (j & 2) ? (w >> 16) : (w & 0xffffu);
     }
-    // every cell of the group is real and matches inside the image
-    const bool interior = D == Dp && x >= Dp - 1;   // uniform per group
+    // winner: minimum key (S << 9) | d over the group, so ties go to the smallest d
+    uint32_t key[DPT];
     uint32_t kmin = 0xffffffffu;
-    if (interior) {
 #pragma unroll
-        for (int j = 0; j < DPT; j++) kmin = min(kmin, (S[j] << 9) | (uint32_t)(d0 + j));
-    } else {
-#pragma unroll
-        for (int j = 0; j < DPT; j++) {
-            const int d = d0 + j;
-            if (d < D) kmin = min(kmin, (S[j] << 9) | (uint32_t)d);
-        }
+    for (int j = 0; j < DPT; j++) {
+        key[j] = (S[j] << 9) + (uint32_t)(d0 + j);
+        if (DFULL || d0 + j < D) kmin = min(kmin, key[j]);
     }
     kmin = group_min<G>(kmin);
     const int ds = (int)(kmin & 511u);
@@ -155,39 +157,42 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
 
     // uniqueness: (100 - u) S(d) < 100 S(d*)  <=>  S(d) < T = ceil(100 S(d*) / (100 - u)),
     // the division done as a multiply-high by umagic = floor(2^32 / (100 - u)) + 1,
-    // exact for numerators below 2^18; 100 - u = 1 (no magic in 32 bits) divides by one
+    // exact for numerators below 2^18; 100 - u = 1 (no magic in 32 bits) divides by one.
+    // The lane compares the minimum over its real cells at least 2 away from d*.
     bool bad = false;
     if (uniq > 0) {
         const uint32_t num = 100u * smin + (uint32_t)(99 - uniq);
         const uint32_t T = uniq == 99 ? num : __umulhi(num, umagic);
+        uint32_t m = 0xffffffffu;
 #pragma unroll
         for (int j = 0; j < DPT; j++) {
             const int d = d0 + j;
-            if ((uint32_t)(d - ds + 1) > 2u && d < D && S[j] < T) bad = true;
+            if ((uint32_t)(d - ds + 1) > 2u && (DFULL || d < D)) m = min(m, S[j]);
         }
+        bad = m < T;
     }
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
     bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
 
     if (act) {
-        if (interior) {
-            if constexpr (DPT == 8) {
-                *reinterpret_cast<uint4*>(sw + d0) =
-                    make_uint4(S[0] | (S[1] << 16), S[2] | (S[3] << 16), S[4] | (S[5] << 16), S[6] | (S[7] << 16));
-            } else {
+        if constexpr (DPT == 8) {
+            *reinterpret_cast<uint4*>(sw + d0) =
+                make_uint4(__byte_perm(ev[0], od[0], 0x5410), __byte_perm(ev[0], od[0], 0x7632),
+                           __byte_perm(ev[1], od[1], 0x5410), __byte_perm(ev[1], od[1], 0x7632));
+        } else {
 #pragma unroll
-                for (int j = 0; j < DPT; j++) sw[d0 + j] = (uint16_t)S[j];
-            }
+            for (int j = 0; j < DPT; j++) sw[d0 + j] = (uint16_t)S[j];
+        }
+        // offers to the right view: right pixel x - d keeps the minimum key
+        if (x >= Dp - 1) {                     // every cell maps inside the image
 #pragma unroll
-            for (int j = 0; j < DPT; j++) atomicMin(&keyR[kr(x - d0 - j)], (S[j] << 9) | (uint32_t)(d0 + j));
+            for (int j = 0; j < DPT; j++)
+                if (DFULL || d0 + j < D) atomicMin(&keyR[kr(x - d0 - j)], key[j]);
         } else {
 #pragma unroll
             for (int j = 0; j < DPT; j++) {
                 const int d = d0 + j;
-                if (d < D) {
-                    sw[d] = (uint16_t)S[j];
-                    if (d <= x) atomicMin(&keyR[kr(x - d)], (S[j] << 9) | (uint32_t)d);
-                }
+                if ((DFULL || d < D) && d <= x) atomicMin(&keyR[kr(x - d)], key[j]);
             }
         }
         if (dbg.aggregated) {
@@ -197,50 +202,47 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
         }
     }
     __syncwarp();
+    // the winner and the parabola's samples for the row's epilogue:
+    // info = S(d*) << 16 | failed uniqueness << 15 | parabola fitted << 14 | d*,
+    // fit = S(d*-1) | S(d*+1) << 16
     if (gl == 0 && act) {
-        float df = (float)ds;
-        if (subpixel && ds >= 1 && ds <= D - 2) {
-            const int sm = sw[ds - 1], sp = sw[ds + 1], s0 = (int)smin;
-            df = (float)ds + __fdiv_rn((float)(sm - sp), (float)(2 * (sm + sp - 2 * s0)));
-        }
-        dispf[x] = df;
-        dstar[x] = (int16_t)ds;
-        ufail[x] = bad ? 1 : 0;
+        const bool para = subpixel && ds >= 1 && ds <= D - 2;
+        info[x] = (smin << 16) | (bad ? 0x8000u : 0u) | (para ? 0x4000u : 0u) | (uint32_t)ds;
+        if (para) fit[x] = (uint32_t)sw[ds - 1] | ((uint32_t)sw[ds + 1] << 16);
     }
     __syncwarp();
 }
 
 // Shared-memory bytes of the block: stage ring, barriers, and per-row arrays.
-template <int NP, int G>
+template <int NP, int G, int THREADS>
 size_t select_smem(int W, int paths, int stages)
 {
     constexpr int Dp = G * 2 * NP;
-    constexpr int kPix = kSelWarps * (32 / G);
+    constexpr int kPix = THREADS / 32 * (32 / G);
     const size_t ring = (size_t)stages * kPix * paths * Dp;
-    return ring + 8 * kMaxStages + (size_t)(W + W / 32) * 4 + (size_t)W * (4 + 2 + 1) + (size_t)kPix * Dp * 2 + 64;
+    return ring + 8 * kMaxStages + (size_t)(W + W / 32) * 4 + (size_t)W * (4 + 4) + (size_t)kPix * Dp * 2 + 64;
 }
 
 // Items are (pair, row); blocks are persistent over them.
-template <int NP, int G, int N>
-__global__ void __launch_bounds__(kSelThreads, 2)
-sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, int uniq, uint32_t umagic,
+template <int NP, int G, int PATHS, int THREADS, int N>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
+sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, uint32_t umagic,
                   int lr_max_diff, int subpixel, float fb, SelectDebug dbg, int* __restrict__ status,
                   int kStages)
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
     constexpr int SPW = 32 / G;                 // pixels a warp takes per stage
-    constexpr int kPix = kSelWarps * SPW;       // pixels per stage
+    constexpr int kPix = THREADS / 32 * SPW;    // pixels per stage
     extern __shared__ __align__(128) uint8_t smem[];
-    const size_t pbytes = (size_t)paths * Dp;   // one pixel's path costs
-    const size_t stage_bytes = kPix * pbytes;
+    constexpr size_t pbytes = (size_t)PATHS * Dp;   // one pixel's path costs
+    constexpr size_t stage_bytes = kPix * pbytes;
     uint8_t* ring = smem;                                              // stages x stage_bytes (multiple of 256)
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * stage_bytes);
     uint16_t* sbuf = reinterpret_cast<uint16_t*>(bars + kMaxStages);   // kPix x Dp, 16-byte aligned
     uint32_t* keyR = reinterpret_cast<uint32_t*>(sbuf + kPix * Dp);    // W + W/32 (padded)
-    float* dispf = reinterpret_cast<float*>(keyR + kr(W));             // W
-    int16_t* dstar = reinterpret_cast<int16_t*>(dispf + W);            // W
-    uint8_t* ufail = reinterpret_cast<uint8_t*>(dstar + W);            // W
+    uint32_t* info = keyR + kr(W);                                     // W
+    uint32_t* fit = info + W;                                          // W
     __shared__ int abort_flag;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -267,14 +269,19 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, i
                            rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
             }
         }
-        for (int i = threadIdx.x; i < kr(W); i += kSelThreads) keyR[i] = 0xffffffffu;
+        for (int i = threadIdx.x; i < kr(W); i += THREADS) keyR[i] = 0xffffffffu;
         __syncthreads();
         for (int st = 0; st < nst; st++, seq++) {
             const int k = seq % kStages;
             if (!stage_wait(&bars[k], (seq / kStages) & 1u)) abort_flag = 1;
             const int x = st * kPix + slot_pix;
-            select_pixel<NP, G>(ring + k * stage_bytes + slot_pix * pbytes, x, x < W, y, W, D, paths, uniq,
-                                umagic, subpixel, gl, sw, keyR, dispf, dstar, ufail, dbg);
+            const uint8_t* src = ring + k * stage_bytes + slot_pix * pbytes;
+            if (D == Dp)
+                select_pixel<NP, G, PATHS, true>(src, x, x < W, y, W, D, uniq, umagic, subpixel, gl, sw, keyR,
+                                                 info, fit, dbg);
+            else
+                select_pixel<NP, G, PATHS, false>(src, x, x < W, y, W, D, uniq, umagic, subpixel, gl, sw, keyR,
+                                                  info, fit, dbg);
             __syncthreads();                    // everyone is done with slot k
             if (abort_flag) {
                 if (threadIdx.x == 0) {
@@ -290,10 +297,17 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, i
                 stage_load(&bars[k], ring + k * stage_bytes, rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
             }
         }
-        for (int x = threadIdx.x; x < W; x += kSelThreads) {
+        for (int x = threadIdx.x; x < W; x += THREADS) {
             const size_t pix = (size_t)y * W + x;
-            const int ds = dstar[x];
-            int m = ufail[x];
+            const uint32_t in = info[x];
+            const int ds = (int)(in & 511u);
+            int m = (in & 0x8000u) ? 1 : 0;
+            float df = (float)ds;
+            if (in & 0x4000u) {                // parabola through S(d*-1), S(d*), S(d*+1)
+                const uint32_t fv = fit[x];
+                const int sm = (int)(fv & 0xffffu), sp = (int)(fv >> 16), s0 = (int)(in >> 16);
+                df = (float)ds + __fdiv_rn((float)(sm - sp), (float)(2 * (sm + sp - 2 * s0)));
+            }
             if (lr_max_diff >= 0) {
                 const int xr = x - ds;
                 if (xr < 0) {
@@ -304,7 +318,6 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int paths, int W, int H, int D, i
                     if (diff > lr_max_diff) m |= 2;
                 }
             }
-            const float df = dispf[x];
             if (!(df > 0.0f)) m |= 4;
             depth[pix] = m == 0 ? __fdiv_rn(fb, df) : 0.0f;
             if (dbg.disparity_int) dbg.disparity_int[pix] = (int16_t)ds;
@@ -344,6 +357,61 @@ cudaError_t dev_limits(DevLimits& out)
     return cudaSuccess;
 }
 
+template <int NP, int G, int PATHS, int THREADS, int N>
+cudaError_t select_launch(const Params& p, const PairTable<N>& pt, int n, const SelectDebug& dbg, int* status,
+                          cudaStream_t s)
+{
+    DevLimits lim;
+    cudaError_t e = dev_limits(lim);
+    if (e != cudaSuccess) return e;
+    // 1024 / THREADS blocks per SM with the deepest ring that lets them fit
+    constexpr int blocks_per_sm = 1024 / THREADS;
+    const size_t budget = blocks_per_sm == 1 ? (size_t)lim.optin : (size_t)lim.per_sm / blocks_per_sm - 1024;
+    int stages = kMaxStages;
+    while (stages > 2 && select_smem<NP, G, THREADS>(p.W, PATHS, stages) > budget) stages--;
+    const size_t smem = select_smem<NP, G, THREADS>(p.W, PATHS, stages);
+    if (smem > budget) return cudaErrorInvalidValue;
+    auto kernel = sgm_select_kernel<NP, G, PATHS, THREADS, N>;
+    e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
+    if (e != cudaSuccess) return e;
+    const int items = n * p.H;
+    const int grid = items < blocks_per_sm * lim.nsm ? items : blocks_per_sm * lim.nsm;   // persistent over rows
+    const uint32_t umagic = (p.uniq > 0 && p.uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
+    kernel<<<grid, THREADS, smem, s>>>(pt, n, p.W, p.H, p.D, p.uniq, umagic, p.lr_max_diff, p.subpixel, p.fb, dbg,
+                                       status, stages);
+    return cudaGetLastError();
+}
+
+template <int NP, int G, int N>
+cudaError_t select_chunk(const Params& p, const PairPtrs* pairs, int n, const Tuning& t,
+                         const SelectDebug& dbg, int* status, cudaStream_t s)
+{
+    PairTable<N> pt{};
+    for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
+    // select_blocks 1: one block of 1024 threads per SM (rows spread over
+    // fewer, faster blocks); 2: two blocks of 512 threads per SM
+    if (p.paths == 4)
+        return t.select_blocks == 1 ? select_launch<NP, G, 4, 1024, N>(p, pt, n, dbg, status, s)
+                                    : select_launch<NP, G, 4, 512, N>(p, pt, n, dbg, status, s);
+    return t.select_blocks == 1 ? select_launch<NP, G, 8, 1024, N>(p, pt, n, dbg, status, s)
+                                : select_launch<NP, G, 8, 512, N>(p, pt, n, dbg, status, s);
+}
+
+template <int N>
+cudaError_t select_dp(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, const SelectDebug& dbg,
+                      int* status, cudaStream_t s)
+{
+    switch (p.Dp) {
+        case 64: return select_chunk<4, 8, N>(p, pairs, n, t, dbg, status, s);
+        case 128: return select_chunk<4, 16, N>(p, pairs, n, t, dbg, status, s);
+        case 192: return select_chunk<3, 32, N>(p, pairs, n, t, dbg, status, s);
+        case 256: return select_chunk<4, 32, N>(p, pairs, n, t, dbg, status, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
 // Raises a kernel's dynamic shared-memory limit when a launch needs more than
 // any earlier launch of that kernel on this device (setting it on every
 // launch would put a function-attribute call between concurrent launches of
@@ -373,54 +441,6 @@ cudaError_t ensure_smem(const void* kernel, size_t bytes)
     else if (used < kMaxEntries) table[used++] = Entry{dev, kernel, bytes};
     return cudaSuccess;
 }
-
-template <int NP, int G, int N>
-cudaError_t select_chunk(const Params& p, const PairPtrs* pairs, int n, const Tuning& t,
-                         const SelectDebug& dbg, int* status, cudaStream_t s)
-{
-    PairTable<N> pt{};
-    for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
-    DevLimits lim;
-    cudaError_t e = dev_limits(lim);
-    if (e != cudaSuccess) return e;
-    const int nsm = lim.nsm, optin = lim.optin, per_sm = lim.per_sm;
-    // t.select_blocks blocks per SM with the deepest ring that lets them fit,
-    // else one block per SM with up to kMaxStages stages
-    int blocks_per_sm = t.select_blocks == 1 ? 1 : 2, stages = kMaxStages;
-    if (blocks_per_sm == 2) {
-        const size_t half = (size_t)per_sm / 2 - 1024;
-        while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > half) stages--;
-        if (select_smem<NP, G>(p.W, p.paths, stages) > half) blocks_per_sm = 1, stages = kMaxStages;
-    }
-    if (blocks_per_sm == 1)
-        while (stages > 2 && select_smem<NP, G>(p.W, p.paths, stages) > (size_t)optin) stages--;
-    const size_t smem = select_smem<NP, G>(p.W, p.paths, stages);
-    if (smem > (size_t)optin) return cudaErrorInvalidValue;
-    e = ensure_smem(reinterpret_cast<const void*>(sgm_select_kernel<NP, G, N>), smem);
-    if (e != cudaSuccess) return e;
-    const int items = n * p.H;
-    const int grid = items < blocks_per_sm * nsm ? items : blocks_per_sm * nsm;   // persistent over rows
-    const uint32_t umagic = (p.uniq > 0 && p.uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
-    sgm_select_kernel<NP, G, N><<<grid, kSelThreads, smem, s>>>(pt, n, p.paths, p.W, p.H, p.D, p.uniq, umagic,
-                                                                p.lr_max_diff, p.subpixel, p.fb, dbg, status,
-                                                                stages);
-    return cudaGetLastError();
-}
-
-template <int N>
-cudaError_t select_dp(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, const SelectDebug& dbg,
-                      int* status, cudaStream_t s)
-{
-    switch (p.Dp) {                            // the path kernel's lane groups
-        case 64: return select_chunk<4, 8, N>(p, pairs, n, t, dbg, status, s);
-        case 128: return select_chunk<4, 16, N>(p, pairs, n, t, dbg, status, s);
-        case 192: return select_chunk<3, 32, N>(p, pairs, n, t, dbg, status, s);
-        case 256: return select_chunk<4, 32, N>(p, pairs, n, t, dbg, status, s);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-}  // namespace
 
 cudaError_t launch_select(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, const SelectDebug& dbg,
                           int* status, cudaStream_t s)

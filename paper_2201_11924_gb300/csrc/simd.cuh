@@ -4,7 +4,8 @@
 // are at most 255, penalties at most 255, the "infinite" neighbour is 0x3FFF
 // plus a penalty), so a plain 32-bit add or subtract of two packed pairs never
 // carries or borrows across the halves and equals two independent 16-bit
-// operations.  min.u16x2 is a native instruction on sm_103a.
+// operations.  min.u16x2 and the three-input __vimin3_u16x2 are native
+// instructions on sm_103a.
 #pragma once
 
 #include <stdint.h>
@@ -17,6 +18,9 @@ __device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b)
     asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
+
+// three-input minimum per half (a DPX instruction on this GPU: one issue slot)
+__device__ __forceinline__ uint32_t vmin3(uint32_t a, uint32_t b, uint32_t c) { return __vimin3_u16x2(a, b, c); }
 
 __device__ __forceinline__ uint32_t vmax2(uint32_t a, uint32_t b)
 {

@@ -174,14 +174,14 @@ int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* p
     }
     if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return SIMSENSE_ERR_CUDA; }
 
-    // one allocation: per pair left codes | right codes | cost | path volume
+    // one allocation: per pair left codes | right codes | cost | work counter | path volume
     std::vector<size_t> off(n);
     size_t total = 0;
     for (int i = 0; i < n; i++) {
         const Params& p = b->classes[cls[i]].p;
         const size_t npx = (size_t)p.W * p.H;
         off[i] = total;
-        total += 2 * round256(npx * (p.wide_codes ? 8 : 4)) + round256(npx * p.Dp) +
+        total += 2 * round256(npx * (p.wide_codes ? 8 : 4)) + round256(npx * p.Dp) + 256 +
                  round256(npx * p.paths * p.Dp);
     }
     bool ok = cudaMalloc(&b->scratch, total) == cudaSuccess && cudaMalloc((void**)&b->status, sizeof(int)) == cudaSuccess &&
@@ -202,7 +202,8 @@ int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* p
         pp.codes_left = base;
         pp.codes_right = base + cb;
         pp.cost = base + 2 * cb;
-        pp.vol = pp.cost + round256(npx * p.Dp);
+        pp.work = reinterpret_cast<uint32_t*>(pp.cost + round256(npx * p.Dp));
+        pp.vol = pp.cost + round256(npx * p.Dp) + 256;
         pp.left = pp.right = nullptr;
         pp.depth = nullptr;
     }
@@ -302,7 +303,7 @@ int simsense_batch_get_tuning(simsense_batch_t b, int c, int* prefetch, int* sel
 int simsense_batch_set_tuning(simsense_batch_t b, int c, int prefetch, int select_blocks)
 {
     if (!b || c < 0 || c >= (int)b->classes.size()) return SIMSENSE_ERR_INVALID_ARG;
-    if (prefetch != 4 && prefetch != 8 && prefetch != 12) return SIMSENSE_ERR_INVALID_ARG;
+    if (prefetch != 8 && prefetch != 12 && prefetch != 16) return SIMSENSE_ERR_INVALID_ARG;
     if (select_blocks != 1 && select_blocks != 2) return SIMSENSE_ERR_INVALID_ARG;
     b->classes[c].tune.prefetch = prefetch;
     b->classes[c].tune.select_blocks = select_blocks;
@@ -324,7 +325,7 @@ int simsense_batch_tune(simsense_batch_t b, const uint8_t* const* left, const ui
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     cudaError_t e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    static const int kPrefetch[3] = {4, 8, 12};
+    static const int kPrefetch[3] = {8, 12, 16};
     for (auto& c : b->classes) {
         Tuning best = c.tune;
         float best_ms = -1.0f;

@@ -99,9 +99,9 @@ def test_tuning_changes_no_result(lib):
         chosen = b.tune(L, R, Z, reps=1)
         assert len(chosen) == b.num_classes()
         for c, t in enumerate(chosen):
-            assert t["prefetch"] in (4, 8, 12) and t["select_blocks"] in (1, 2)
+            assert t["prefetch"] in (8, 12, 16) and t["select_blocks"] in (1, 2)
         for c in range(b.num_classes()):
-            for pf, sb in ((4, 1), (12, 2)):
+            for pf, sb in ((8, 1), (16, 2)):
                 b.set_tuning(c, pf, sb)
                 for z in Z:
                     z.fill_(0.0)
