@@ -161,7 +161,7 @@ int simsense_compute_debug(simsense_t h, const uint8_t* left_u8, const uint8_t* 
  * library's code, held until the process exits).  It calls no cudaMalloc,
  * cudaFree or allocating library routine.
  *   - The problem must fit: 2 * round256(W*H*code bytes)
- *     + round256(W*H*Dp) + 256 + paths*W*H*Dp <= SIMSENSE_NOALLOC_SCRATCH_BYTES,
+ *     + round256(W*H*Dp) + paths*W*H*Dp <= SIMSENSE_NOALLOC_SCRATCH_BYTES,
  *     with code bytes = 4 when w*h - 1 <= 32 else 8, and Dp = 64 * ceil(D/64).  Larger problems, like
  *     any other out-of-range argument, return SIMSENSE_ERR_INVALID_ARG.
  *     (320x240, D = 64, 4 paths fits; 1280x720 does not.)

@@ -36,7 +36,6 @@ struct Scratch {
     uint8_t* cost = nullptr;       // H x W x Dp uint8, Hamming cost C
     uint8_t* paths = nullptr;      // H x W x paths x Dp uint8, L_r per path
     int* status = nullptr;         // device status word (SIMSENSE_ERR_TIMEOUT after a bounded wait gave up)
-    uint32_t* work = nullptr;      // work counter of the path kernel (zeroed before each launch)
     uint8_t* stage_left = nullptr; // host-call staging: H x W uint8
     uint8_t* stage_right = nullptr;
     float* stage_depth = nullptr;  // H x W float32
@@ -53,8 +52,6 @@ struct PairPtrs {
     uint8_t* cost;           // H x W x Dp
     uint8_t* vol;            // H x W x paths x Dp
     float* depth;            // H x W
-    uint32_t* work;          // 4-byte work counter of the path kernel; a launch over
-                             // several pairs uses the first pair's
 };
 
 // Pairs of one launch, passed by value as a kernel parameter (nothing to

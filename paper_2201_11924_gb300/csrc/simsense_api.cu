@@ -38,7 +38,6 @@ void free_scratch(Scratch& s)
     cudaFree(s.cost);
     cudaFree(s.paths);
     cudaFree(s.status);
-    cudaFree(s.work);
     cudaFree(s.stage_left);
     cudaFree(s.stage_right);
     cudaFree(s.stage_depth);
@@ -68,7 +67,7 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
 {
     const Params& p = h->p;
     Scratch& s = h->s;
-    const PairPtrs pair{left, right, s.codes_left, s.codes_right, s.cost, s.paths, depth, s.work};
+    const PairPtrs pair{left, right, s.codes_left, s.codes_right, s.cost, s.paths, depth};
     const Tuning tune{};
     cudaError_t e = mark(h, SIMSENSE_STAGE_CENSUS, false, st);
     if (e == cudaSuccess) e = launch_census(p, &pair, 1, st);
@@ -171,7 +170,6 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
               cudaMalloc((void**)&s.paths, vol_bytes) == cudaSuccess &&
               cudaMalloc((void**)&s.status, sizeof(int)) == cudaSuccess &&
               cudaMemset(s.status, 0, sizeof(int)) == cudaSuccess &&
-              cudaMalloc((void**)&s.work, sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc((void**)&s.stage_left, npx) == cudaSuccess &&
               cudaMalloc((void**)&s.stage_right, npx) == cudaSuccess &&
               cudaMalloc((void**)&s.stage_depth, npx * sizeof(float)) == cudaSuccess;
@@ -181,7 +179,7 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
         delete h;
         return SIMSENSE_ERR_OOM;
     }
-    s.bytes = 2 * code_bytes + cost_bytes + vol_bytes + 2 * npx + npx * sizeof(float) + sizeof(uint32_t);
+    s.bytes = 2 * code_bytes + cost_bytes + vol_bytes + 2 * npx + npx * sizeof(float);
     *out = h;
     return SIMSENSE_OK;
 }

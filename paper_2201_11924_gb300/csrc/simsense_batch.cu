@@ -174,14 +174,14 @@ int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* p
     }
     if (cudaGetDevice(&b->device) != cudaSuccess) { delete b; return SIMSENSE_ERR_CUDA; }
 
-    // one allocation: per pair left codes | right codes | cost | work counter | path volume
+    // one allocation: per pair left codes | right codes | cost | path volume
     std::vector<size_t> off(n);
     size_t total = 0;
     for (int i = 0; i < n; i++) {
         const Params& p = b->classes[cls[i]].p;
         const size_t npx = (size_t)p.W * p.H;
         off[i] = total;
-        total += 2 * round256(npx * (p.wide_codes ? 8 : 4)) + round256(npx * p.Dp) + 256 +
+        total += 2 * round256(npx * (p.wide_codes ? 8 : 4)) + round256(npx * p.Dp) +
                  round256(npx * p.paths * p.Dp);
     }
     bool ok = cudaMalloc(&b->scratch, total) == cudaSuccess && cudaMalloc((void**)&b->status, sizeof(int)) == cudaSuccess &&
@@ -202,8 +202,7 @@ int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* p
         pp.codes_left = base;
         pp.codes_right = base + cb;
         pp.cost = base + 2 * cb;
-        pp.work = reinterpret_cast<uint32_t*>(pp.cost + round256(npx * p.Dp));
-        pp.vol = pp.cost + round256(npx * p.Dp) + 256;
+        pp.vol = pp.cost + round256(npx * p.Dp);
         pp.left = pp.right = nullptr;
         pp.depth = nullptr;
     }

@@ -72,12 +72,12 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
     int rc = make_params(p, W, H, D, census_win, P1, P2, paths, uniq_ratio, lr_max_diff, f, baseline, subpixel);
     if (rc != SIMSENSE_OK) return rc;
 
-    // carve the fixed array: left codes | right codes | cost volume | work counter | path volume
+    // carve the fixed array: left codes | right codes | cost volume | path volume
     const size_t npx = (size_t)W * H;
     const size_t code_bytes = round256(npx * (p.wide_codes ? 8 : 4));
     const size_t cost_bytes = round256(npx * p.Dp);
     const size_t vol_bytes = (size_t)paths * npx * p.Dp;
-    if (2 * code_bytes + cost_bytes + 256 + vol_bytes > (size_t)SIMSENSE_NOALLOC_SCRATCH_BYTES)
+    if (2 * code_bytes + cost_bytes + vol_bytes > (size_t)SIMSENSE_NOALLOC_SCRATCH_BYTES)
         return SIMSENSE_ERR_INVALID_ARG;
     void* base = nullptr;
     rc = scratch_address(&base);
@@ -86,11 +86,10 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
     void* codes_left = b;
     void* codes_right = b + code_bytes;
     uint8_t* cost = b + 2 * code_bytes;
-    uint32_t* work = reinterpret_cast<uint32_t*>(cost + cost_bytes);
-    uint8_t* vol = cost + cost_bytes + 256;
+    uint8_t* vol = cost + cost_bytes;
 
     cudaStream_t st = (cudaStream_t)stream;
-    const PairPtrs pair{left_u8, right_u8, codes_left, codes_right, cost, vol, depth_f32, work};
+    const PairPtrs pair{left_u8, right_u8, codes_left, codes_right, cost, vol, depth_f32};
     const Tuning tune{};
     const SelectDebug none{};
     cudaError_t e = launch_census(p, &pair, 1, st);
