@@ -44,26 +44,40 @@ census_kernel(PairTable<N> pt, int W, int H, int ww_rt, int wh_rt)
     const int x = blockIdx.x * kTX + threadIdx.x, y = blockIdx.y * kTY + threadIdx.y;
     if (x >= W || y >= H) return;
     const uint8_t* t = tile + threadIdx.y * kTileW + threadIdx.x;
-    const uint8_t c = t[ry * kTileW + rx];
-    CodeT code = 0;
+    const int c = t[ry * kTileW + rx];
+    // bit = [I(neighbour) < I(centre)] is the sign bit of the difference; the
+    // code is built MSB first in raster order, the leading nbits - 32 bits
+    // (64-bit codes) in the high word
+    uint32_t hi = 0, lo = 0;
     if constexpr (WW > 0) {
+        constexpr int nb = WW * WH - 1;
+        int b = 0;
 #pragma unroll
         for (int dy = 0; dy < WH; dy++) {
 #pragma unroll
             for (int dx = 0; dx < WW; dx++) {
                 if (dy == WH / 2 && dx == WW / 2) continue;
-                code = (code << 1) | (CodeT)(t[dy * kTileW + dx] < c ? 1u : 0u);
+                const uint32_t bit = (uint32_t)((int)t[dy * kTileW + dx] - c) >> 31;
+                if (nb - b > 32) hi = (hi << 1) | bit;
+                else lo = (lo << 1) | bit;
+                b++;
             }
         }
     } else {
+        const int nb = ww * wh - 1;
+        int b = 0;
         for (int dy = 0; dy < wh; dy++) {
             for (int dx = 0; dx < ww; dx++) {
                 if (dy == ry && dx == rx) continue;
-                code = (code << 1) | (CodeT)(t[dy * kTileW + dx] < c ? 1u : 0u);
+                const uint32_t bit = (uint32_t)((int)t[dy * kTileW + dx] - c) >> 31;
+                if (nb - b > 32) hi = (hi << 1) | bit;
+                else lo = (lo << 1) | bit;
+                b++;
             }
         }
     }
-    out[(size_t)y * W + x] = code;
+    if constexpr (sizeof(CodeT) == 8) out[(size_t)y * W + x] = ((uint64_t)hi << 32) | lo;
+    else out[(size_t)y * W + x] = lo;
 }
 
 __global__ void widen_kernel(const uint32_t* __restrict__ in, uint64_t* __restrict__ out, size_t n)

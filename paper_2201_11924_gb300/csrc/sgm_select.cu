@@ -257,45 +257,55 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, ui
     }
     __syncthreads();
 
-    uint32_t seq = 0;                           // stages consumed by this block so far
+    // ring slot and barrier phase of the next stage to consume (stage number
+    // seq of this block lives in slot seq % kStages, phase (seq / kStages) & 1;
+    // both are advanced incrementally)
+    int slot = 0;
+    uint32_t phase = 0;
     for (int item = blockIdx.x; item < npairs * H; item += gridDim.x) {
         const int pair = item / H, y = item - pair * H;
         const uint8_t* rowsrc = pt.p[pair].vol + (size_t)y * W * pbytes;
         float* __restrict__ depth = pt.p[pair].depth;
         if (threadIdx.x == 0) {
-            for (int k = 0; k < kStages && k < nst; k++) {
+            for (int k = 0, s = slot; k < kStages && k < nst; k++, s = s + 1 == kStages ? 0 : s + 1) {
                 const int x0 = k * kPix, n = min(kPix, W - x0);
-                stage_load(&bars[(seq + k) % kStages], ring + ((seq + k) % kStages) * stage_bytes,
-                           rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
+                stage_load(&bars[s], ring + s * stage_bytes, rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
             }
         }
         for (int i = threadIdx.x; i < kr(W); i += THREADS) keyR[i] = 0xffffffffu;
         __syncthreads();
-        for (int st = 0; st < nst; st++, seq++) {
-            const int k = seq % kStages;
-            if (!stage_wait(&bars[k], (seq / kStages) & 1u)) abort_flag = 1;
+        for (int st = 0; st < nst; st++) {
+            if (!stage_wait(&bars[slot], phase)) abort_flag = 1;
             const int x = st * kPix + slot_pix;
-            const uint8_t* src = ring + k * stage_bytes + slot_pix * pbytes;
+            const uint8_t* src = ring + slot * stage_bytes + slot_pix * pbytes;
             if (D == Dp)
                 select_pixel<NP, G, PATHS, true>(src, x, x < W, y, W, D, uniq, umagic, subpixel, gl, sw, keyR,
                                                  info, fit, dbg);
             else
                 select_pixel<NP, G, PATHS, false>(src, x, x < W, y, W, D, uniq, umagic, subpixel, gl, sw, keyR,
                                                   info, fit, dbg);
-            __syncthreads();                    // everyone is done with slot k
+            __syncthreads();                    // everyone is done with this slot
             if (abort_flag) {
                 if (threadIdx.x == 0) {
                     if (status) atomicExch(status, SIMSENSE_ERR_TIMEOUT);
-                    // drain the copies still in flight into this block's ring (bounded)
-                    for (int j = 1; j < kStages && st + j < nst; j++)
-                        stage_wait(&bars[(seq + j) % kStages], ((seq + j) / kStages) & 1u);
+                    // drain the copies still in flight into this block's ring
+                    // (bounded), this stage's own included: its wait may be
+                    // the one that gave up
+                    int s = slot;
+                    uint32_t ph = phase;
+                    for (int j = 0; j < kStages && st + j < nst; j++) {
+                        stage_wait(&bars[s], ph);
+                        if (++s == kStages) { s = 0; ph ^= 1u; }
+                    }
                 }
                 return;
             }
             if (threadIdx.x == 0 && st + kStages < nst) {
                 const int x0 = (st + kStages) * kPix, n = min(kPix, W - x0);
-                stage_load(&bars[k], ring + k * stage_bytes, rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
+                stage_load(&bars[slot], ring + slot * stage_bytes, rowsrc + (size_t)x0 * pbytes,
+                           (uint32_t)(n * pbytes));
             }
+            if (++slot == kStages) { slot = 0; phase ^= 1u; }
         }
         for (int x = threadIdx.x; x < W; x += THREADS) {
             const size_t pix = (size_t)y * W + x;
