@@ -33,7 +33,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2201_11924_gb300 import configs, scenes  # noqa: E402
+from paper_2201_11924_gb300 import configs, replicas, scenes  # noqa: E402
 
 METRIC = "depth_frames_per_s"
 UNIT = "frames/s"
@@ -359,20 +359,17 @@ def main():
     import torch
     from paper_2201_11924_gb300 import simsense
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", local if world > 1 else 0)
+    # one replica per GPU: no data-path collective, only the timing barrier
+    # and the maximum of the ranks' elapsed times
+    rep = replicas.from_env()
+    world, rank = rep.world, rep.rank
+    dev = torch.device("cuda", rep.local)
     torch.cuda.set_device(dev)
 
-    # a few distinct seeded pairs per rank, resident in HBM
+    # a few distinct seeded pairs per rank, resident in HBM: rank r owns pairs
+    # r, r + N, r + 2N, ... of the job (weak scaling, nothing shared)
     n_pairs = 4
-    pairs = [scenes.make_pair(wl, seed=wl.seed + 1000 * rank + i) for i in range(n_pairs)]
+    pairs = [scenes.make_pair(wl, seed=wl.seed + u) for u in replicas.shard(world * n_pairs, rank, world)]
     lefts = [torch.from_numpy(p["left"]).to(dev) for p in pairs]
     rights = [torch.from_numpy(p["right"]).to(dev) for p in pairs]
     depth = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
@@ -385,8 +382,7 @@ def main():
     m.set_option(simsense.OPT_PROFILE, 1)
 
     sampler = ClockSampler(_bus_id(torch, dev))
-    if dist:
-        dist.barrier()
+    rep.barrier()
     torch.cuda.synchronize()
     t_wall0 = time.time()
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -396,17 +392,13 @@ def main():
         m.compute(lefts[i % n_pairs], rights[i % n_pairs], depth)
     ev1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    rep.barrier()
     t_wall1 = time.time()
     clocks = sampler.stop(t_wall0, t_wall1)
     el_ms = ev0.elapsed_time(ev1)
     stage_ms, n_prof = m.profile_read()
     m.set_option(simsense.OPT_PROFILE, 0)
-    if dist:
-        t = torch.tensor([el_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
+    el_ms = rep.max_over_ranks(el_ms, dev)
     value = world * args.steps / (el_ms / 1e3)
 
     # end to end through the host-buffer call: pinned inputs in, depth out
@@ -416,8 +408,7 @@ def main():
     for i in range(args.warmup):
         m.compute_host(hl[i % n_pairs], hr[i % n_pairs], hd)
         stream.synchronize()
-    if dist:
-        dist.barrier()
+    rep.barrier()
     e2e_steps = max(3, min(args.steps, 500))
     t0 = time.perf_counter()
     for i in range(e2e_steps):
@@ -425,10 +416,7 @@ def main():
         stream.synchronize()
         _ = float(hd[0, 0])
     e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = rep.max_over_ranks(e2e_s, dev)
     e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 2 * wl.W * wl.H, "d2h_bytes_per_step": 4 * wl.W * wl.H,
            "steps": e2e_steps}
@@ -446,8 +434,7 @@ def main():
                 bt.compute(bl, br, bd)
             torch.cuda.synchronize()
             bsteps = max(3, args.steps // nb)
-            if dist:
-                dist.barrier()
+            rep.barrier()
             b0 = torch.cuda.Event(enable_timing=True)
             b1 = torch.cuda.Event(enable_timing=True)
             b0.record(stream)
@@ -457,18 +444,14 @@ def main():
             torch.cuda.synchronize()
             b_ms = b0.elapsed_time(b1)
             status = bt.device_status()
-        if dist:
-            t = torch.tensor([b_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            b_ms = float(t.item())
+        b_ms = rep.max_over_ranks(b_ms, dev)
         batched = {"value": world * nb * bsteps / (b_ms / 1e3), "unit": UNIT, "pairs_per_batch": nb,
                    "batches": bsteps, "ms_per_batch": b_ms / bsteps, "graph": True,
                    "device_status": status}
 
     if rank != 0:
         m.close()
-        if dist:
-            dist.destroy_process_group()
+        rep.close()
         return 0
 
     # roofline of the dominant kernel, from the live stage events
@@ -512,8 +495,7 @@ def main():
     }
     print(json.dumps(line), flush=True)
     m.close()
-    if dist:
-        dist.destroy_process_group()
+    rep.close()
     return 0
 
 
