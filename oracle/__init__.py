@@ -59,8 +59,14 @@ def _load():
             lib.oracle_select.argtypes = [P, I, I, I, I, I, I, Dd, P, P, P, P]
             lib.oracle_compute.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, I, Dd, Dd,
                                            P, P, P, P, P, P, P]
+            lib.oracle_census_cs.argtypes = [P, I, I, I, I, P]
+            lib.oracle_cost_block.argtypes = [P, I, I, I, I, I, P]
+            lib.oracle_median.argtypes = [P, I, I, I, P]
+            lib.oracle_compute_ex.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, I, Dd, Dd, I, I, I, I,
+                                              P, P, P, P, P, P, P]
             for fn in ("oracle_census", "oracle_cost", "oracle_path", "oracle_aggregate",
-                       "oracle_select", "oracle_compute"):
+                       "oracle_select", "oracle_compute", "oracle_census_cs", "oracle_cost_block",
+                       "oracle_median", "oracle_compute_ex"):
                 getattr(lib, fn).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -128,12 +134,41 @@ def select(S: np.ndarray, uniq: int, lr_max_diff: int, subpixel: bool, fb: float
     return dstar, mask, disp, depth
 
 
+def census_cs(img: np.ndarray, ww: int, wh: int) -> np.ndarray:
+    """Centre-symmetric census codes ((ww*wh-1)/2 bits) of one view (uint64, H x W)."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape
+    out = np.empty((H, W), dtype=np.uint64)
+    _check(_load().oracle_census_cs(_ptr(img), W, H, ww, wh, _ptr(out)), "census_cs")
+    return out
+
+
+def cost_block(C: np.ndarray, bw: int, bh: int) -> np.ndarray:
+    """SGBM block cost: the mean of C over a bw x bh block, rounded half up (uint8, H x W x D)."""
+    C = np.ascontiguousarray(C, dtype=np.uint8)
+    H, W, D = C.shape
+    out = np.empty((H, W, D), dtype=np.uint8)
+    _check(_load().oracle_cost_block(_ptr(C), W, H, D, bw, bh, _ptr(out)), "cost_block")
+    return out
+
+
+def median(img: np.ndarray, k: int) -> np.ndarray:
+    """k x k median of a float map with replicated borders (float64, H x W)."""
+    img = np.ascontiguousarray(img, dtype=np.float64)
+    H, W = img.shape
+    out = np.empty((H, W), dtype=np.float64)
+    _check(_load().oracle_median(_ptr(img), W, H, k, _ptr(out)), "median")
+    return out
+
+
 def compute(left, right, D, ww, wh, P1, P2, paths, uniq, lr_max_diff, subpixel, f, baseline,
-            want_codes=False, want_S=False):
+            want_codes=False, want_S=False, census_cs=False, block=(1, 1), median=0):
     """The whole stage for one pair.  Returns a dict of numpy arrays.
 
     ``f`` and ``baseline`` are converted to float32 first, as the library
-    receives them, and their product is then formed in fp64.
+    receives them, and their product is then formed in fp64.  census_cs,
+    block = (bw, bh) and median = k select the variants (centre-symmetric
+    census, SGBM block cost, k x k median filter).
     """
     left = np.ascontiguousarray(left, dtype=np.uint8)
     right = np.ascontiguousarray(right, dtype=np.uint8)
@@ -149,10 +184,11 @@ def compute(left, right, D, ww, wh, P1, P2, paths, uniq, lr_max_diff, subpixel, 
     cl = np.empty((H, W), dtype=np.uint64) if want_codes else None
     cr = np.empty((H, W), dtype=np.uint64) if want_codes else None
     S = np.empty((H, W, D), dtype=np.int32) if want_S else None
-    rc = _load().oracle_compute(_ptr(left), _ptr(right), W, H, D, ww, wh, P1, P2, paths, uniq,
-                                lr_max_diff, int(bool(subpixel)), f32, b32,
-                                _ptr(out["depth"]), _ptr(out["disp"]), _ptr(out["dstar"]),
-                                _ptr(out["mask"]), _ptr(cl), _ptr(cr), _ptr(S))
+    rc = _load().oracle_compute_ex(_ptr(left), _ptr(right), W, H, D, ww, wh, P1, P2, paths, uniq,
+                                   lr_max_diff, int(bool(subpixel)), f32, b32, int(bool(census_cs)),
+                                   int(block[0]), int(block[1]), int(median),
+                                   _ptr(out["depth"]), _ptr(out["disp"]), _ptr(out["dstar"]),
+                                   _ptr(out["mask"]), _ptr(cl), _ptr(cr), _ptr(S))
     _check(rc, "compute")
     if want_codes:
         out["codes_left"], out["codes_right"] = cl, cr

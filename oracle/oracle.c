@@ -43,6 +43,21 @@
  *  - depth: Z = f b / d_f for a valid pixel with d_f > 0, else 0.
  *  - mask bits: 1 = uniqueness failed, 2 = left-right failed,
  *    4 = d_f <= 0.  A pixel is valid iff its mask is 0.
+ *
+ * Variants Sec. VI-D also names (optional in the stage):
+ *  - centre-symmetric census (CSCT): for every offset o of the window that
+ *    precedes the centre in raster order, bit = [I(p+o) < I(p-o)]; a pair
+ *    with a pixel outside the image gives 0; (w h - 1) / 2 bits, first
+ *    offset = most significant bit.
+ *  - SGBM block cost: the per-pixel Hamming cost averaged over a bw x bh
+ *    block around the pixel (same d), over the block's pixels inside the
+ *    image, rounded half up: Cb = floor((sum + n/2) / n).  The paper gives
+ *    no normalisation; the mean keeps the cost within [0, nbits], the range
+ *    the path costs are bounded with.
+ *  - median filter: the k x k median of the disparity map after the checks
+ *    (invalid pixels count as 0, borders replicated); the output pixel is
+ *    valid iff the median is > 0, with depth f b / median.  The mask keeps
+ *    the bits of the checks before the filter.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -245,18 +260,109 @@ int oracle_select(const int32_t* S, int W, int H, int D, int uniq, int lr_max_di
     return ORACLE_OK;
 }
 
+/* ------------------------------------------------------------- variants */
+
+/* Centre-symmetric census transform of one view (the census variant Sec.
+ * VI-D names).  img: H x W bytes; codes: H x W uint64. */
+int oracle_census_cs(const uint8_t* img, int W, int H, int ww, int wh, uint64_t* codes)
+{
+    if (!img || !codes || W <= 0 || H <= 0) return ORACLE_BAD_ARG;
+    if (ww < 1 || wh < 1 || (ww % 2) == 0 || (wh % 2) == 0) return ORACLE_BAD_ARG;
+    if ((ww * wh - 1) / 2 > 64) return ORACLE_BAD_ARG;
+    int rx = ww / 2, ry = wh / 2;
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            uint64_t code = 0;
+            for (int dy = -ry; dy <= ry; dy++) {
+                for (int dx = -rx; dx <= rx; dx++) {
+                    /* only the offsets before the centre: each pair once */
+                    if (dy > 0 || (dy == 0 && dx >= 0)) continue;
+                    int ax = x + dx, ay = y + dy;   /* p + o */
+                    int bx = x - dx, by = y - dy;   /* p - o */
+                    int bit = 0;
+                    if (ax >= 0 && ax < W && ay >= 0 && ay < H && bx >= 0 && bx < W && by >= 0 && by < H)
+                        bit = img[ay * W + ax] < img[by * W + bx] ? 1 : 0;
+                    code = (code << 1) | (uint64_t)bit;
+                }
+            }
+            codes[y * W + x] = code;
+        }
+    }
+    return ORACLE_OK;
+}
+
+/* SGBM block cost (Sec. VI-D: SGBM compares the local regions of the two
+ * pixels): the mean of C over the bw x bh block centred on each pixel, over
+ * the block's pixels inside the image, rounded half up.
+ * C, Cb: H x W x D bytes (Cb must not alias C). */
+int oracle_cost_block(const uint8_t* C, int W, int H, int D, int bw, int bh, uint8_t* Cb)
+{
+    if (!C || !Cb || W <= 0 || H <= 0 || D <= 0) return ORACLE_BAD_ARG;
+    if (bw < 1 || bh < 1 || (bw % 2) == 0 || (bh % 2) == 0) return ORACLE_BAD_ARG;
+    int rx = bw / 2, ry = bh / 2;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++)
+            for (int d = 0; d < D; d++) {
+                int sum = 0, n = 0;
+                for (int v = -ry; v <= ry; v++)
+                    for (int u = -rx; u <= rx; u++) {
+                        int xx = x + u, yy = y + v;
+                        if (xx < 0 || xx >= W || yy < 0 || yy >= H) continue;
+                        sum += C[((size_t)yy * W + xx) * D + d];
+                        n++;
+                    }
+                Cb[((size_t)y * W + x) * D + d] = (uint8_t)((sum + n / 2) / n);
+            }
+    return ORACLE_OK;
+}
+
+/* k x k median of a disparity map with replicated borders (Sec. VI-D lists
+ * median filtering among the disparity post-processing steps).
+ * in, out: H x W doubles (out must not alias in). */
+int oracle_median(const double* in, int W, int H, int k, double* out)
+{
+    if (!in || !out || W <= 0 || H <= 0 || k < 1 || (k % 2) == 0 || k > 9) return ORACLE_BAD_ARG;
+    int r = k / 2;
+    double win[81];
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            int n = 0;
+            for (int v = -r; v <= r; v++)
+                for (int u = -r; u <= r; u++) {
+                    int xx = x + u, yy = y + v;
+                    if (xx < 0) xx = 0;
+                    if (xx >= W) xx = W - 1;
+                    if (yy < 0) yy = 0;
+                    if (yy >= H) yy = H - 1;
+                    win[n++] = in[yy * W + xx];
+                }
+            /* insertion sort; the median is the middle of the k*k values */
+            for (int i = 1; i < n; i++) {
+                double t = win[i];
+                int j = i - 1;
+                while (j >= 0 && win[j] > t) { win[j + 1] = win[j]; j--; }
+                win[j + 1] = t;
+            }
+            out[y * W + x] = win[n / 2];
+        }
+    return ORACLE_OK;
+}
+
 /* ------------------------------------------------------------ whole stage */
 
-/* The whole depth stage for one rectified pair.  Every output except depth
- * may be NULL.  codes: H x W; cost: H x W x D bytes; S: H x W x D int32. */
-int oracle_compute(const uint8_t* left, const uint8_t* right, int W, int H, int D,
-                   int ww, int wh, int P1, int P2, int paths, int uniq, int lr_max_diff,
-                   int subpixel, double f, double baseline,
-                   double* depth, double* disp, int32_t* dstar, uint8_t* mask,
-                   uint64_t* codes_left, uint64_t* codes_right, int32_t* S_out)
+/* The whole depth stage for one rectified pair, with the optional variants:
+ * census_cs = 1 selects the centre-symmetric census, bw x bh > 1 x 1 the SGBM
+ * block cost, median_k > 1 the median filter.  Every output except depth may
+ * be NULL.  codes: H x W; S: H x W x D int32. */
+int oracle_compute_ex(const uint8_t* left, const uint8_t* right, int W, int H, int D,
+                      int ww, int wh, int P1, int P2, int paths, int uniq, int lr_max_diff,
+                      int subpixel, double f, double baseline, int census_cs, int bw, int bh, int median_k,
+                      double* depth, double* disp, int32_t* dstar, uint8_t* mask,
+                      uint64_t* codes_left, uint64_t* codes_right, int32_t* S_out)
 {
     if (!left || !right || !depth || W <= 0 || H <= 0 || D <= 0) return ORACLE_BAD_ARG;
-    int nbits = ww * wh - 1;
+    if (bw < 1 || bh < 1 || median_k < 0) return ORACLE_BAD_ARG;
+    int nbits = census_cs ? (ww * wh - 1) / 2 : ww * wh - 1;
     size_t npx = (size_t)W * H, nvol = npx * (size_t)D;
     uint64_t* cl = codes_left ? codes_left : (uint64_t*)malloc(npx * sizeof(uint64_t));
     uint64_t* cr = codes_right ? codes_right : (uint64_t*)malloc(npx * sizeof(uint64_t));
@@ -265,12 +371,52 @@ int oracle_compute(const uint8_t* left, const uint8_t* right, int W, int H, int 
     int32_t* ds = dstar ? dstar : (int32_t*)malloc(npx * sizeof(int32_t));
     int rc = ORACLE_OK;
     if (!cl || !cr || !C || !S || !ds) { rc = ORACLE_NO_MEMORY; goto done; }
-    rc = oracle_census(left, W, H, ww, wh, cl);
-    if (rc == ORACLE_OK) rc = oracle_census(right, W, H, ww, wh, cr);
+    if (census_cs) {
+        rc = oracle_census_cs(left, W, H, ww, wh, cl);
+        if (rc == ORACLE_OK) rc = oracle_census_cs(right, W, H, ww, wh, cr);
+    } else {
+        rc = oracle_census(left, W, H, ww, wh, cl);
+        if (rc == ORACLE_OK) rc = oracle_census(right, W, H, ww, wh, cr);
+    }
     if (rc == ORACLE_OK) rc = oracle_cost(cl, cr, W, H, D, nbits, C);
+    if (rc == ORACLE_OK && (bw > 1 || bh > 1)) {
+        uint8_t* Cb = (uint8_t*)malloc(nvol);
+        if (!Cb) { rc = ORACLE_NO_MEMORY; goto done; }
+        rc = oracle_cost_block(C, W, H, D, bw, bh, Cb);
+        memcpy(C, Cb, nvol);
+        free(Cb);
+    }
     if (rc == ORACLE_OK) rc = oracle_aggregate(C, W, H, D, paths, P1, P2, S);
-    if (rc == ORACLE_OK)
-        rc = oracle_select(S, W, H, D, uniq, lr_max_diff, subpixel, f * baseline, ds, mask, disp, depth);
+    if (rc == ORACLE_OK) {
+        double* dsp = (double*)malloc(npx * sizeof(double));
+        uint8_t* msk = (uint8_t*)malloc(npx);
+        if (!dsp || !msk) {
+            free(dsp);
+            free(msk);
+            rc = ORACLE_NO_MEMORY;
+            goto done;
+        }
+        rc = oracle_select(S, W, H, D, uniq, lr_max_diff, subpixel, f * baseline, ds, msk, dsp, depth);
+        if (rc == ORACLE_OK && median_k > 1) {
+            /* invalid pixels enter the filter as 0 */
+            double* d0 = (double*)malloc(npx * sizeof(double));
+            if (!d0) {
+                rc = ORACLE_NO_MEMORY;
+            } else {
+                for (size_t i = 0; i < npx; i++) d0[i] = msk[i] == 0 ? dsp[i] : 0.0;
+                rc = oracle_median(d0, W, H, median_k, dsp);
+                for (size_t i = 0; i < npx && rc == ORACLE_OK; i++) {
+                    depth[i] = dsp[i] > 0.0 ? f * baseline / dsp[i] : 0.0;
+                    if (!(dsp[i] > 0.0)) dsp[i] = -1.0;
+                }
+                free(d0);
+            }
+        }
+        if (disp) memcpy(disp, dsp, npx * sizeof(double));
+        if (mask) memcpy(mask, msk, npx);
+        free(dsp);
+        free(msk);
+    }
 done:
     if (!codes_left) free(cl);
     if (!codes_right) free(cr);
@@ -278,4 +424,15 @@ done:
     if (!S_out) free(S);
     if (!dstar) free(ds);
     return rc;
+}
+
+/* The plain stage (full census, per-pixel cost, no median filter). */
+int oracle_compute(const uint8_t* left, const uint8_t* right, int W, int H, int D,
+                   int ww, int wh, int P1, int P2, int paths, int uniq, int lr_max_diff,
+                   int subpixel, double f, double baseline,
+                   double* depth, double* disp, int32_t* dstar, uint8_t* mask,
+                   uint64_t* codes_left, uint64_t* codes_right, int32_t* S_out)
+{
+    return oracle_compute_ex(left, right, W, H, D, ww, wh, P1, P2, paths, uniq, lr_max_diff, subpixel, f,
+                             baseline, 0, 1, 1, 0, depth, disp, dstar, mask, codes_left, codes_right, S_out);
 }
