@@ -70,6 +70,33 @@ typedef struct simsense_ctx* simsense_t;
 /* options for simsense_set_option */
 #define SIMSENSE_OPT_SUBPIXEL       1     /* value 0/1, default 1 */
 #define SIMSENSE_OPT_PROFILE        2     /* value 0/1, default 0: time each stage */
+/*
+ * Variants of the stage that Sec. VI-D names (arxiv 2201.11924: SimSense
+ * "performs a center-symmetric census transform", "also supports semi-global
+ * block matching (SGBM)" whose cost is "the hamming distance between the local
+ * regions of the two pixels", and lists "median filtering" among the
+ * disparity post-processing steps).  The paper defines none of them; the
+ * library's readings:
+ *  CENSUS_CS  value 0/1, default 0.  1: for every window offset o before the
+ *             centre in raster order, bit = [I(p+o) < I(p-o)], a pair with a
+ *             pixel outside the image gives 0; (w*h-1)/2 bits, first offset
+ *             = most significant bit.
+ *  BLOCK      value bw | bh << 8 (odd, 1..7 each), default 1 | 1 << 8 (per-
+ *             pixel cost).  Otherwise the cost of (x, y, d) is the per-pixel
+ *             Hamming cost averaged over the bw x bh block around (x, y) at
+ *             the same d, over the block's pixels inside the image, rounded
+ *             half up (the mean keeps the cost within [0, nbits]).
+ *  MEDIAN     value 0, 3 or 5, default 0.  k x k median of the disparity map
+ *             after the checks (invalid pixels count as 0, borders
+ *             replicated); a pixel is valid iff the median is > 0, depth =
+ *             f*b / median.  The debug disparity is the filtered one; the
+ *             debug mask keeps the bits of the checks before the filter.
+ * Out-of-range values return SIMSENSE_ERR_INVALID_ARG and change nothing.
+ * The batch and no-allocation entry points run the plain stage only.
+ */
+#define SIMSENSE_OPT_CENSUS_CS      3
+#define SIMSENSE_OPT_BLOCK          4
+#define SIMSENSE_OPT_MEDIAN         5
 
 /* stages timed under SIMSENSE_OPT_PROFILE, in launch order */
 #define SIMSENSE_STAGE_CENSUS       0     /* census transform of both views */

@@ -52,10 +52,16 @@ class Workload:
     baseline: float = 0.055      # metres
     seed: int = 0
     scene: Scene = field(default_factory=Scene)
+    # variants Sec. VI-D names: centre-symmetric census, SGBM block (bw, bh),
+    # k x k median filter (0 = off)
+    census_cs: bool = False
+    block: tuple = (1, 1)
+    median: int = 0
 
     @property
     def nbits(self) -> int:
-        return self.win_w * self.win_h - 1
+        full = self.win_w * self.win_h - 1
+        return full // 2 if self.census_cs else full
 
     @property
     def census_win(self) -> int:

@@ -99,7 +99,74 @@ cudaError_t cost_code(const Params& p, const PairPtrs* pairs, int n, cudaStream_
     return cost_chunk<uint32_t, N>(p, pairs, n, s);
 }
 
+// SGBM block cost (the variant Sec. VI-D describes: the Hamming distance
+// between the local regions of the two pixels): the per-pixel cost volume
+// `raw` averaged over the bw x bh block around each pixel (same d), over the
+// block's pixels inside the image, rounded half up, into `out`.  A thread
+// takes one 4-byte word (4 disparities) of one pixel: the block sum of each
+// byte is accumulated as two 16-bit pairs (at most 49 x 255 < 2^16), and the
+// division by the pixel count n is a multiply-high by floor(2^32 / n) + 1,
+// exact for every numerator below 2^16 and n <= 81.
+struct Magic {
+    uint32_t m[82];
+};
+
+template <int N>
+__global__ void __launch_bounds__(256)
+block_cost_kernel(PairTable<N> pt, int W, int H, int Dp, int bw, int bh, Magic mg)
+{
+    const int words = Dp >> 2;                         // words per pixel
+    const int ppb = 256 / words;                       // pixels per block
+    if (threadIdx.x >= ppb * words) return;          // Dp = 192: 5 pixels x 48 words
+    const int x = blockIdx.x * ppb + threadIdx.x / words;
+    const int w = threadIdx.x % words;
+    const int y = blockIdx.y;
+    if (x >= W) return;
+    const uint32_t* __restrict__ raw = reinterpret_cast<const uint32_t*>(pt.p[blockIdx.z].vol);
+    uint32_t* __restrict__ out = reinterpret_cast<uint32_t*>(pt.p[blockIdx.z].cost);
+    const int rx = bw >> 1, ry = bh >> 1;
+    const int x0 = max(x - rx, 0), x1 = min(x + rx, W - 1);
+    const int y0 = max(y - ry, 0), y1 = min(y + ry, H - 1);
+    uint32_t ev = 0, od = 0;                           // (b0, b2) and (b1, b3) sums
+    for (int yy = y0; yy <= y1; yy++) {
+        const uint32_t* row = raw + ((size_t)yy * W) * words + w;
+        for (int xx = x0; xx <= x1; xx++) {
+            const uint32_t v = __ldg(row + (size_t)xx * words);
+            ev += v & 0x00ff00ffu;
+            od += (v >> 8) & 0x00ff00ffu;
+        }
+    }
+    const uint32_t n = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
+    const uint32_t m = mg.m[n], h = n >> 1;
+    const uint32_t c0 = __umulhi((ev & 0xffffu) + h, m), c2 = __umulhi((ev >> 16) + h, m);
+    const uint32_t c1 = __umulhi((od & 0xffffu) + h, m), c3 = __umulhi((od >> 16) + h, m);
+    out[((size_t)y * W + x) * words + w] = c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
+}
+
+template <int N>
+cudaError_t block_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
+{
+    PairTable<N> pt{};
+    for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
+    Magic mg{};
+    for (uint32_t k = 1; k < 82; k++) mg.m[k] = (uint32_t)(0x100000000ull / k) + 1u;
+    const int ppb = 256 / (p.Dp / 4);
+    dim3 grid((p.W + ppb - 1) / ppb, p.H, n);
+    block_cost_kernel<N><<<grid, 256, 0, s>>>(pt, p.W, p.H, p.Dp, p.block_w, p.block_h, mg);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+cudaError_t launch_block_cost(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
+{
+    for (int b = 0; b < n; b += kMaxBatch) {
+        const int c = n - b < kMaxBatch ? n - b : kMaxBatch;
+        cudaError_t e = c == 1 ? block_chunk<1>(p, pairs + b, 1, s) : block_chunk<kMaxBatch>(p, pairs + b, c, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_cost(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
 {

@@ -27,7 +27,16 @@ struct Params {
     int dpt;                 // disparities per lane of a 32-lane scanline group (2, 4, 6, 8)
     int Dp;                  // padded disparity pitch = 32 * dpt
     bool wide_codes;         // census codes need 64 bits (nbits > 32)
+    // variants (Sec. VI-D): centre-symmetric census, SGBM block cost over
+    // block_w x block_h (1 x 1 = per-pixel cost), median filter (0 = off, 3, 5)
+    int census_cs = 0;
+    int block_w = 1, block_h = 1;
+    int median = 0;
 };
+
+// Applies a variant option to p (re-deriving nbits and the code width) after
+// checking the ranges; returns a SIMSENSE status.
+int set_variant(Params& p, int opt, int value);
 
 // Device scratch of one handle (all owned by the handle).
 struct Scratch {
@@ -87,6 +96,12 @@ struct SelectDebug {
 cudaError_t launch_census(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s);
 cudaError_t launch_widen_codes(const Params& p, const void* codes, uint64_t* out, cudaStream_t s);
 cudaError_t launch_cost(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s);
+// SGBM block cost: pairs[i].vol holds the per-pixel cost volume on entry,
+// pairs[i].cost receives its block mean.
+cudaError_t launch_block_cost(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s);
+// k x k median filter of the disparity map disp (invalid = 0) into depth,
+// and the filtered disparity (invalid = -1) into disp_out when it is not null.
+cudaError_t launch_median(const Params& p, const float* disp, float* depth, float* disp_out, cudaStream_t s);
 cudaError_t launch_paths(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s);
 cudaError_t launch_select(const Params& p, const PairPtrs* pairs, int n, const Tuning& t,
                           const SelectDebug& dbg, int* status, cudaStream_t s);

@@ -94,13 +94,6 @@ __device__ __forceinline__ uint32_t group_min(uint32_t v)
     return v;
 }
 
-__device__ __forceinline__ uint32_t vmin2(uint32_t a, uint32_t b)
-{
-    uint32_t d;
-    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-
 // One pixel of the row for one lane group: sum, winner, uniqueness, offers to
 // the right view, parabola.  src is the pixel's first path in the stage.
 // DFULL: D equals the padded range, so every cell is a real disparity.
@@ -228,7 +221,7 @@ template <int NP, int G, int PATHS, int THREADS, int N>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, uint32_t umagic,
                   int lr_max_diff, int subpixel, float fb, SelectDebug dbg, int* __restrict__ status,
-                  int kStages)
+                  int kStages, int disp_mode)
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
@@ -329,7 +322,9 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, ui
                 }
             }
             if (!(df > 0.0f)) m |= 4;
-            depth[pix] = m == 0 ? __fdiv_rn(fb, df) : 0.0f;
+            // disp_mode (a median filter follows): the disparity, 0 when invalid
+            if (disp_mode) depth[pix] = m == 0 ? df : 0.0f;
+            else depth[pix] = m == 0 ? __fdiv_rn(fb, df) : 0.0f;
             if (dbg.disparity_int) dbg.disparity_int[pix] = (int16_t)ds;
             if (dbg.disparity) dbg.disparity[pix] = m == 0 ? df : -1.0f;
             if (dbg.mask) dbg.mask[pix] = (uint8_t)m;
@@ -388,7 +383,7 @@ cudaError_t select_launch(const Params& p, const PairTable<N>& pt, int n, const 
     const int grid = items < blocks_per_sm * lim.nsm ? items : blocks_per_sm * lim.nsm;   // persistent over rows
     const uint32_t umagic = (p.uniq > 0 && p.uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
     kernel<<<grid, THREADS, smem, s>>>(pt, n, p.W, p.H, p.D, p.uniq, umagic, p.lr_max_diff, p.subpixel, p.fb, dbg,
-                                       status, stages);
+                                       status, stages, p.median > 1 ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -74,7 +74,16 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_CENSUS, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     e = mark(h, SIMSENSE_STAGE_COST, false, st);
-    if (e == cudaSuccess) e = launch_cost(p, &pair, 1, st);
+    if (p.block_w > 1 || p.block_h > 1) {
+        // SGBM: the per-pixel costs go to the path volume (free until the
+        // path stage), their block mean to the cost volume
+        PairPtrs raw = pair;
+        raw.cost = s.paths;
+        if (e == cudaSuccess) e = launch_cost(p, &raw, 1, st);
+        if (e == cudaSuccess) e = launch_block_cost(p, &pair, 1, st);
+    } else if (e == cudaSuccess) {
+        e = launch_cost(p, &pair, 1, st);
+    }
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_COST, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     e = mark(h, SIMSENSE_STAGE_PATHS, false, st);
@@ -89,7 +98,16 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
         sd.mask = dbg->mask;
     }
     e = mark(h, SIMSENSE_STAGE_SELECT, false, st);
-    if (e == cudaSuccess) e = launch_select(p, &pair, 1, tune, sd, s.status, st);
+    if (p.median > 1) {
+        // the selection writes the disparity into the cost volume (free after
+        // the path stage), the median filter turns it into depth
+        PairPtrs sel = pair;
+        sel.depth = reinterpret_cast<float*>(s.cost);
+        if (e == cudaSuccess) e = launch_select(p, &sel, 1, tune, sd, s.status, st);
+        if (e == cudaSuccess) e = launch_median(p, sel.depth, depth, sd.disparity, st);
+    } else if (e == cudaSuccess) {
+        e = launch_select(p, &pair, 1, tune, sd, s.status, st);
+    }
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_SELECT, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
     if (h->prof.on && h->prof.count < ProfileRing::kSlots) h->prof.count++;
@@ -139,6 +157,36 @@ int make_params(Params& p, int W, int H, int D, int census_win, int P1, int P2, 
     p.Dp = 32 * p.dpt;
     p.wide_codes = nbits > 32;
     return SIMSENSE_OK;
+}
+
+int set_variant(Params& p, int opt, int value)
+{
+    switch (opt) {
+        case SIMSENSE_OPT_CENSUS_CS: {
+            if (value != 0 && value != 1) return SIMSENSE_ERR_INVALID_ARG;
+            const int full = p.win_w * p.win_h - 1;
+            const int nbits = value ? full / 2 : full;
+            if (nbits < 1 || nbits + p.P2 > 255) return SIMSENSE_ERR_INVALID_ARG;
+            p.census_cs = value;
+            p.nbits = nbits;
+            p.wide_codes = nbits > 32;
+            return SIMSENSE_OK;
+        }
+        case SIMSENSE_OPT_BLOCK: {
+            const int bw = value & 0xff, bh = (value >> 8) & 0xff;
+            if ((value >> 16) != 0 || bw < 1 || bh < 1 || bw > 7 || bh > 7 || !(bw & 1) || !(bh & 1))
+                return SIMSENSE_ERR_INVALID_ARG;
+            p.block_w = bw;
+            p.block_h = bh;
+            return SIMSENSE_OK;
+        }
+        case SIMSENSE_OPT_MEDIAN:
+            if (value != 0 && value != 3 && value != 5) return SIMSENSE_ERR_INVALID_ARG;
+            p.median = value;
+            return SIMSENSE_OK;
+        default:
+            return SIMSENSE_ERR_INVALID_ARG;
+    }
 }
 
 }  // namespace simsense
@@ -242,6 +290,10 @@ int simsense_set_option(simsense_t h, int opt, int value)
             r.count = 0;
             return SIMSENSE_OK;
         }
+        case SIMSENSE_OPT_CENSUS_CS:
+        case SIMSENSE_OPT_BLOCK:
+        case SIMSENSE_OPT_MEDIAN:
+            return set_variant(h->p, opt, value);
         default:
             return SIMSENSE_ERR_INVALID_ARG;
     }

@@ -21,6 +21,9 @@ ERR_CUDA = -3
 ERR_TIMEOUT = -4
 OPT_SUBPIXEL = 1
 OPT_PROFILE = 2
+OPT_CENSUS_CS = 3
+OPT_BLOCK = 4
+OPT_MEDIAN = 5
 STAGES = ("census", "cost", "paths", "select")
 
 _lock = threading.Lock()
@@ -118,8 +121,19 @@ class SimSense:
 
     @classmethod
     def from_workload(cls, wl):
-        return cls(wl.W, wl.H, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq,
-                   wl.lr_max_diff, wl.f, wl.baseline, subpixel=wl.subpixel)
+        m = cls(wl.W, wl.H, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq,
+                wl.lr_max_diff, wl.f, wl.baseline, subpixel=wl.subpixel)
+        m.set_variant(census_cs=getattr(wl, "census_cs", False), block=getattr(wl, "block", (1, 1)),
+                      median=getattr(wl, "median", 0))
+        return m
+
+    def set_variant(self, census_cs: bool = False, block=(1, 1), median: int = 0):
+        """Selects the variants of the stage (centre-symmetric census, SGBM
+        block cost over block = (bw, bh), k x k median filter; defaults =
+        the plain stage)."""
+        self.set_option(OPT_CENSUS_CS, int(bool(census_cs)))
+        self.set_option(OPT_BLOCK, int(block[0]) | (int(block[1]) << 8))
+        self.set_option(OPT_MEDIAN, int(median))
 
     def _check(self, rc, what):
         if rc != OK:
