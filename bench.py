@@ -20,6 +20,7 @@ frames by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import datetime
 import json
 import os
@@ -64,11 +65,15 @@ def algorithmic_ops(wl):
     4 nbits / D."""
     cells = wl.W * wl.H * wl.D
     cost = 5 if wl.nbits > 32 else 2
+    bw, bh = getattr(wl, "block", (1, 1))
+    if bw * bh > 1:
+        cost += bw * bh + 1          # SGBM: the block sum and the rounded division
+    k = getattr(wl, "median", 0)
     return {
         "census": wl.W * wl.H * 4 * wl.nbits,
         "cost": cells * cost,
         "paths": cells * 7 * wl.paths,
-        "select": cells * (wl.paths + 6),
+        "select": cells * (wl.paths + 6) + wl.W * wl.H * k * k * (k * k // 2 + 1) * (2 if k else 0),
     }
 
 
@@ -157,7 +162,8 @@ def cpu_oracle_rate(wl, pair, budget_s=10.0, strip_rows=90):
         l = pair["left"][y0:y0 + strip_rows]
         r = pair["right"][y0:y0 + strip_rows]
         oracle.compute(l, r, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq,
-                       wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline)
+                       wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline, census_cs=wl.census_cs,
+                       block=wl.block, median=wl.median)
         cells += wl.W * l.shape[0] * wl.D
         n += 1
         el = time.perf_counter() - t0
@@ -178,7 +184,8 @@ def run_reference(args, wl):
     def step(i):
         y0 = (i * strip) % max(1, wl.H - strip + 1)
         oracle.compute(pair["left"][y0:y0 + strip], pair["right"][y0:y0 + strip], wl.D, wl.win_w, wl.win_h,
-                       wl.P1, wl.P2, wl.paths, wl.uniq, wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline)
+                       wl.P1, wl.P2, wl.paths, wl.uniq, wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline,
+                       census_cs=wl.census_cs, block=wl.block, median=wl.median)
 
     for i in range(args.warmup):
         step(i)
@@ -343,11 +350,21 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4, help="compute slots per size class")
     ap.add_argument("--serve-sustain", type=float, default=1200.0,
                     help="second, below-capacity arrival rate for the latency figures")
+    ap.add_argument("--census-cs", action="store_true", help="variant: centre-symmetric census")
+    ap.add_argument("--block", default="1x1", help="variant: SGBM block, e.g. 3x3 (1x1 = per-pixel cost)")
+    ap.add_argument("--median", type=int, default=0, choices=[0, 3, 5], help="variant: k x k median filter")
     ap.add_argument("--batch-pairs", type=int, default=8,
                     help="pairs per batch for the batched sub-measurement of the plain workload")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = configs.ALL[args.workload]
+    if args.census_cs or args.block != "1x1" or args.median:
+        # a variant of the stage Sec. VI-D names, on the same workload
+        bw, bh = (int(v) for v in args.block.split("x"))
+        wl = dataclasses.replace(wl, census_cs=bool(args.census_cs), block=(bw, bh), median=args.median,
+                                 name=wl.name + ("_csct" if args.census_cs else "") +
+                                 (f"_sgbm{bw}x{bh}" if bw * bh > 1 else "") +
+                                 (f"_median{args.median}" if args.median else ""))
 
     if args.impl == "reference":
         return run_reference(args, wl)
@@ -423,7 +440,8 @@ def main():
 
     # the batched form on the same workload: batch_pairs pairs per CUDA-graph launch
     batched = None
-    if args.batch_pairs > 1:
+    variant = wl.census_cs or wl.block != (1, 1) or wl.median
+    if args.batch_pairs > 1 and not variant:      # the batched form runs the plain stage
         nb = args.batch_pairs
         bwl = [wl] * nb
         bl = [lefts[i % n_pairs] for i in range(nb)]
@@ -481,7 +499,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
         "config": {"workload": wl.name, "W": wl.W, "H": wl.H, "D": wl.D, "paths": wl.paths,
-                   "census": f"{wl.win_w}x{wl.win_h}", "P1": wl.P1, "P2": wl.P2, "uniq": wl.uniq,
+                   "census": f"{wl.win_w}x{wl.win_h}" + (" centre-symmetric" if wl.census_cs else ""),
+                   "block": f"{wl.block[0]}x{wl.block[1]}", "median": wl.median,
+                   "P1": wl.P1, "P2": wl.P2, "uniq": wl.uniq,
                    "lr_max_diff": wl.lr_max_diff, "subpixel": wl.subpixel, "pairs_cycled": n_pairs,
                    "l2": "no flush: every step streams its own ~1 GB path volume through HBM, "
                          "far above the 129 MB L2", "path": "plain (one pair per call)"},

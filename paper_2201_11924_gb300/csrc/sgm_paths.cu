@@ -211,8 +211,7 @@ template <int NQ, int G, int PF, bool Guard>
 __device__ __forceinline__ void walk_steps(int base, int n, int len, uint32_t ring, const uint8_t*& cf,
                                            long long cstep, uint8_t*& op, long long ostep,
                                            uint32_t (&Lc)[2 * NQ], uint32_t (&Lp)[2 * NQ], uint32_t& mm,
-                                           uint32_t p1, uint32_t p2, uint32_t edge_lo, uint32_t edge_hi,
-                                           uint32_t hi8)
+                                           uint32_t p1, uint32_t p2, uint32_t edge_lo, uint32_t edge_hi)
 {
 #pragma unroll
     for (int k = 0; k < PF; k++) {
@@ -235,7 +234,7 @@ __device__ __forceinline__ void walk_steps(int base, int n, int len, uint32_t ri
             const uint32_t tO = vmin3(Lc[2 * q + 1], Lp[2 * q], shift_pair(Lp[2 * q], Enext));
             // cost bytes (c0, c1, c2, c3) -> (c0, c2) and (c1, c3)
             const uint32_t cE = cw[q] & 0x00ff00ffu;
-            const uint32_t cO = __umulhi(cw[q] - cE, hi8);     // (cw - cE) >> 8
+            const uint32_t cO = __byte_perm(cw[q], 0, 0x4341);
             L[2 * q] = tE + cE - mm;           // no borrow: every half of t is >= m'
             L[2 * q + 1] = tO + cO - mm;
             out[q] = L[2 * q + 1] * 256u + L[2 * q];            // bytes (L0, L1, L2, L3)
@@ -261,7 +260,7 @@ __device__ __forceinline__ void walk_steps(int base, int n, int len, uint32_t ri
 // loop) holds 16 bytes per lane, so the warp's ring is PF x 512 bytes.
 template <int NQ, int G, int PF>
 __device__ __forceinline__ void walk(const uint8_t* __restrict__ C, int W, int H, int P1, int P2, int paths,
-                                     uint8_t* __restrict__ vol, int r, int rx, int ry, int scan, uint32_t hi8)
+                                     uint8_t* __restrict__ vol, int r, int rx, int ry, int scan)
 {
     constexpr int DPT = 4 * NQ;
     constexpr int Dp = G * DPT;
@@ -312,10 +311,10 @@ __device__ __forceinline__ void walk(const uint8_t* __restrict__ C, int W, int H
     int base = 0;
     for (; base < nmain; base += PF)
         walk_steps<NQ, G, PF, false>(base, n, len, ring, cf, cstep, op, ostep, Lc, Lp, mm, p1, p2,
-                                     edge_lo, edge_hi, hi8);
+                                     edge_lo, edge_hi);
     for (; base < n; base += PF)
         walk_steps<NQ, G, PF, true>(base, n, len, ring, cf, cstep, op, ostep, Lc, Lp, mm, p1, p2,
-                                    edge_lo, edge_hi, hi8);
+                                    edge_lo, edge_hi);
 }
 
 // Work items of one launch: warp-sized groups of scanlines, longest first.
@@ -351,7 +350,7 @@ __host__ __device__ inline Items make_items(int W, int H, int paths, int npairs,
 // SMs at the end.
 template <int NQ, int G, int NQH, int GH, int PF, int N>
 __global__ void __launch_bounds__(kPathThreads)
-sgm_paths_kernel(PairTable<N> pt, int npairs, int W, int H, int P1, int P2, int paths, uint32_t hi8)
+sgm_paths_kernel(PairTable<N> pt, int npairs, int W, int H, int P1, int P2, int paths)
 {
     static_assert(G * 4 * NQ == GH * 4 * NQH, "both layouts cover the same padded range");
     constexpr int SPW = 32 / G, SPWH = 32 / GH;
@@ -380,11 +379,11 @@ sgm_paths_kernel(PairTable<N> pt, int npairs, int W, int H, int P1, int P2, int 
     int rx, ry;
     path_dir(r, rx, ry);
     if (cls == 0) {
-        walk<NQH, GH, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry, g * SPWH + lane / GH, hi8);
+        walk<NQH, GH, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry, g * SPWH + lane / GH);
     } else {
         const int j = g * SPW + lane / G;
         const int scan = cls == 1 ? j : (j < W + H - 1 ? diag_scan(j, rx, W, H) : W + H - 1);
-        walk<NQ, G, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry, scan, hi8);
+        walk<NQ, G, PF>(C, W, H, P1, P2, paths, vol, r, rx, ry, scan);
     }
 }
 
@@ -400,7 +399,7 @@ cudaError_t paths_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStrea
     auto kernel = sgm_paths_kernel<NQ, G, NQH, GH, PF, N>;
     cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
     if (e != cudaSuccess) return e;
-    kernel<<<blocks, kPathThreads, smem, s>>>(pt, n, p.W, p.H, p.P1, p.P2, p.paths, 1u << 24);
+    kernel<<<blocks, kPathThreads, smem, s>>>(pt, n, p.W, p.H, p.P1, p.P2, p.paths);
     return cudaGetLastError();
 }
 
