@@ -77,6 +77,32 @@ def algorithmic_ops(wl):
     }
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one
+# ncu capture (profiles/ncu_full_1280x720_D128_8path.md), with the SHA-1 of
+# the kernel's source at the time: a changed source reports null.
+MEASURED_TRAFFIC = {
+    "1280x720_D128_census7x7_8path": {
+        "paths": (536795136 + 887504384, "c92b81b5107b142f958ce668184dc6800818212b",
+                  "paper_2201_11924_gb300/csrc/sgm_paths.cu"),
+    },
+}
+
+
+def measured_traffic(wl, kernel):
+    import hashlib
+    ent = MEASURED_TRAFFIC.get(wl.name, {}).get(kernel)
+    if not ent:
+        return None
+    nbytes, sha, src = ent
+    try:
+        with open(os.path.join(ROOT, src), "rb") as fh:
+            if hashlib.sha1(fh.read()).hexdigest() != sha:
+                return None
+    except OSError:
+        return None
+    return nbytes
+
+
 def algorithmic_bytes(wl):
     """HBM bytes per frame the method must move: both views in (2 B/px),
     depth out (4 B/px) and one spilled partial-sum volume between the forward
@@ -482,7 +508,8 @@ def main():
     int_peak = n_sm * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12        # T ops/s
     achieved = ops[dom] / launch_s / 1e12
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": int_peak,
-                "unit": "Tops/s", "frac": achieved / int_peak, "traffic": None,
+                "unit": "Tops/s", "frac": achieved / int_peak, "traffic": measured_traffic(wl, dom),
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": f"derived: {n_sm} SMs x {INT32_LANES_PER_SM} INT32 lanes x {sm_max:.0f} MHz",
                 "stage_ms_per_step": {k: v / max(1, n_prof) for k, v in stage_ms.items()},
                 "hbm_algorithmic_bytes_per_frame": algorithmic_bytes(wl),
