@@ -37,7 +37,7 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -64,9 +64,14 @@ def _load():
             lib.oracle_median.argtypes = [P, I, I, I, P]
             lib.oracle_compute_ex.argtypes = [P, P, I, I, I, I, I, I, I, I, I, I, I, Dd, Dd, I, I, I, I,
                                               P, P, P, P, P, P, P]
+            U64 = ctypes.c_uint64
+            U32 = ctypes.c_uint32
+            lib.oracle_philox4x64.argtypes = [P, P, P]
+            lib.oracle_philox4x64.restype = None
+            lib.oracle_noise.argtypes = [P, I, I, Dd, Dd, Dd, Dd, U64, U32, U32, P, P, P]
             for fn in ("oracle_census", "oracle_cost", "oracle_path", "oracle_aggregate",
                        "oracle_select", "oracle_compute", "oracle_census_cs", "oracle_cost_block",
-                       "oracle_median", "oracle_compute_ex"):
+                       "oracle_median", "oracle_compute_ex", "oracle_noise"):
                 getattr(lib, fn).restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -159,6 +164,34 @@ def median(img: np.ndarray, k: int) -> np.ndarray:
     out = np.empty((H, W), dtype=np.float64)
     _check(_load().oracle_median(_ptr(img), W, H, k, _ptr(out)), "median")
     return out
+
+
+def philox4x64(ctr, key) -> np.ndarray:
+    """Philox4x64-10 of a 4-word counter under a 2-word key (4 uint64)."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.empty(4, dtype=np.uint64)
+    _load().oracle_philox4x64(_ptr(c), _ptr(k), _ptr(out))
+    return out
+
+
+# D415 noise parameters the paper estimates (Sec. VII, sensor parameters)
+D415_NOISE = dict(mu=-0.231, sigma=0.83, k=3.98, theta=0.254)
+
+
+def noise(clean, mu, sigma, k, theta, seed, frame=0, view=0):
+    """Sensor noise of one view (Sec. VI-C).  Returns (noisy uint8, value
+    float64 before rounding, margin float64 = distance of the nearest
+    decision to its threshold)."""
+    clean = np.ascontiguousarray(clean, dtype=np.uint8)
+    H, W = clean.shape
+    noisy = np.empty((H, W), dtype=np.uint8)
+    value = np.empty((H, W), dtype=np.float64)
+    margin = np.empty((H, W), dtype=np.float64)
+    _check(_load().oracle_noise(_ptr(clean), W, H, float(mu), float(sigma), float(k), float(theta),
+                                int(seed), int(frame), int(view), _ptr(value), _ptr(noisy), _ptr(margin)),
+           "noise")
+    return noisy, value, margin
 
 
 def compute(left, right, D, ww, wh, P1, P2, paths, uniq, lr_max_diff, subpixel, f, baseline,

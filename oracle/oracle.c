@@ -44,6 +44,16 @@
  *  - mask bits: 1 = uniqueness failed, 2 = left-right failed,
  *    4 = d_f <= 0.  A pixel is valid iff its mask is 0.
  *
+ * Sensor noise (Sec. VI-C, the step before stereo matching):
+ *    I_noisy = gamma * I_clean + n,  gamma ~ Gamma(k, theta),  n ~ N(mu, sigma^2),
+ *  per pixel and view, then rounded half to even and clamped to [0, 255].
+ *  Random numbers come from the counter-based Philox4x64-10 generator
+ *  (Salmon et al., SC 2011) with counter (pixel, attempt, frame, view) and
+ *  key (seed, 0); a 64-bit output r gives the uniform ((r >> 40) + 1/2) / 2^24.
+ *  Normals by Box-Muller, gamma by Marsaglia and Tsang's squeeze-free
+ *  rejection method (k >= 1), at most 16 attempts (if all are rejected,
+ *  gamma = (k - 1/3) theta).
+ *
  * Variants Sec. VI-D also names (optional in the stage):
  *  - centre-symmetric census (CSCT): for every offset o of the window that
  *    precedes the centre in raster order, bit = [I(p+o) < I(p-o)]; a pair
@@ -59,6 +69,7 @@
  *    valid iff the median is > 0, with depth f b / median.  The mask keeps
  *    the bits of the checks before the filter.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -345,6 +356,78 @@ int oracle_median(const double* in, int W, int H, int k, double* out)
             }
             out[y * W + x] = win[n / 2];
         }
+    return ORACLE_OK;
+}
+
+/* ---------------------------------------------------------- sensor noise */
+
+/* Philox4x64-10: ten rounds of two 64x64->128-bit multiplies with the key
+ * bumped by the Weyl constants between rounds. */
+void oracle_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t out[4])
+{
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint64_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        unsigned __int128 p0 = (unsigned __int128)M0 * x0;
+        unsigned __int128 p1 = (unsigned __int128)M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0;
+        uint64_t hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t y0 = hi1 ^ x1 ^ k0, y1 = lo1, y2 = hi0 ^ x3 ^ k1, y3 = lo0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += W0;
+        k1 += W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+static double unit24(uint64_t r) { return ((double)(r >> 40) + 0.5) / 16777216.0; }
+
+/* Sensor noise of one view (Sec. VI-C).  clean, noisy: H x W bytes.  value
+ * (may be NULL): the noisy intensity before rounding.  margin (may be NULL):
+ * the smallest distance of a decision to its threshold (the rounding of
+ * value and every acceptance test evaluated), for comparisons with a
+ * single-precision implementation. */
+int oracle_noise(const uint8_t* clean, int W, int H, double mu, double sigma, double k, double theta,
+                 uint64_t seed, uint32_t frame, uint32_t view, double* value, uint8_t* noisy, double* margin)
+{
+    if (!clean || !noisy || W <= 0 || H <= 0 || !(k >= 1.0) || !(theta > 0.0) || !(sigma >= 0.0))
+        return ORACLE_BAD_ARG;
+    const double PI = 3.14159265358979323846;
+    const double d = k - 1.0 / 3.0, c = 1.0 / (3.0 * sqrt(d));
+    const uint64_t key[2] = {seed, 0};
+    for (int i = 0; i < W * H; i++) {
+        double gamma = d * theta, z1 = 0.0, m = 1e300;
+        for (int attempt = 0; attempt < 16; attempt++) {
+            const uint64_t ctr[4] = {(uint64_t)i, (uint64_t)attempt, frame, view};
+            uint64_t r[4];
+            oracle_philox4x64(ctr, key, r);
+            double u0 = unit24(r[0]), u1 = unit24(r[1]), u2 = unit24(r[2]);
+            double rad = sqrt(-2.0 * log(u0));
+            double z0 = rad * cos(2.0 * PI * u1);
+            z1 = rad * sin(2.0 * PI * u1);
+            double t = 1.0 + c * z0;
+            if (!(t > 0.0)) continue;
+            double v = t * t * t;
+            double lhs = log(u2), rhs = 0.5 * z0 * z0 + d - d * v + d * log(v);
+            double gap = fabs(lhs - rhs);
+            if (gap < m) m = gap;
+            if (lhs < rhs) {
+                gamma = d * v * theta;
+                break;
+            }
+        }
+        double val = gamma * (double)clean[i] + (mu + sigma * z1);
+        double q = nearbyint(val);            /* round half to even (default mode) */
+        double bgap = fabs(val - (floor(val) + 0.5));
+        if (bgap < m) m = bgap;
+        if (q < 0.0) q = 0.0;
+        if (q > 255.0) q = 255.0;
+        noisy[i] = (uint8_t)q;
+        if (value) value[i] = val;
+        if (margin) margin[i] = m;
+    }
     return ORACLE_OK;
 }
 
