@@ -208,6 +208,35 @@ int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* right_u8, fl
                              int uniq_ratio, int lr_max_diff, float f, float baseline,
                              int subpixel, struct CUstream_st* stream);
 
+/*
+ * IR sensor noise (arxiv 2201.11924 Sec. VI-C): I_noisy = gamma * I_clean + n
+ * per pixel, gamma ~ Gamma(k, theta) (laser speckle), n ~ N(mu, sigma^2)
+ * (thermal noise); the D415 values Sec. VII estimates are mu = -0.231,
+ * sigma = 0.83, k = 3.98, theta = 0.254.  The result is rounded half to even
+ * and clamped to [0, 255].  Random numbers: Philox4x64-10 with counter
+ * (pixel index y*W + x, attempt, frame, view) and key (seed, 0); a 64-bit
+ * output r gives the uniform ((r >> 41) + 1/2) / 2^23; normals by Box-Muller,
+ * gamma by Marsaglia-Tsang rejection (k >= 1, at most 16 attempts).  The paper
+ * fixes neither the generator nor the sampling method.
+ *
+ * simsense_set_noise: enable (1) or disable (0) the noise on both views of
+ * every later compute call of h (views 0 = left, 1 = right); the n-th call
+ * after this one uses frame n.  Requires k >= 1, theta > 0, sigma >= 0, all
+ * finite, when enabling; else SIMSENSE_ERR_INVALID_ARG.  The batch and
+ * no-allocation entry points run without noise.
+ *
+ * simsense_add_noise: the same noise on one device image: clean and noisy
+ * are W x H device bytes (row-major; they may be the same buffer), frame and
+ * view select the generator stream.  Asynchronous on stream;
+ * SIMSENSE_ERR_INVALID_ARG for NULL buffers, W or H < 1, W*H > 2^30 or the
+ * parameter ranges above, SIMSENSE_ERR_CUDA for a failed launch.
+ */
+int simsense_set_noise(simsense_t h, int enable, float mu, float sigma, float k, float theta,
+                       unsigned long long seed);
+int simsense_add_noise(const uint8_t* clean, uint8_t* noisy, int W, int H, float mu, float sigma, float k,
+                       float theta, unsigned long long seed, unsigned int frame, unsigned int view,
+                       struct CUstream_st* stream);
+
 /* Set an option (SIMSENSE_OPT_*).  Takes effect at the next compute call. */
 int simsense_set_option(simsense_t h, int opt, int value);
 

@@ -49,7 +49,7 @@
  *  per pixel and view, then rounded half to even and clamped to [0, 255].
  *  Random numbers come from the counter-based Philox4x64-10 generator
  *  (Salmon et al., SC 2011) with counter (pixel, attempt, frame, view) and
- *  key (seed, 0); a 64-bit output r gives the uniform ((r >> 40) + 1/2) / 2^24.
+ *  key (seed, 0); a 64-bit output r gives the uniform ((r >> 41) + 1/2) / 2^23.
  *  Normals by Box-Muller, gamma by Marsaglia and Tsang's squeeze-free
  *  rejection method (k >= 1), at most 16 attempts (if all are rejected,
  *  gamma = (k - 1/3) theta).
@@ -382,7 +382,8 @@ void oracle_philox4x64(const uint64_t ctr[4], const uint64_t key[2], uint64_t ou
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-static double unit24(uint64_t r) { return ((double)(r >> 40) + 0.5) / 16777216.0; }
+/* uniform in (0, 1) from the top 23 bits: (2m + 1) / 2^24, exact in single precision too */
+static double unit23(uint64_t r) { return ((double)(r >> 41) + 0.5) / 8388608.0; }
 
 /* Sensor noise of one view (Sec. VI-C).  clean, noisy: H x W bytes.  value
  * (may be NULL): the noisy intensity before rounding.  margin (may be NULL):
@@ -403,7 +404,7 @@ int oracle_noise(const uint8_t* clean, int W, int H, double mu, double sigma, do
             const uint64_t ctr[4] = {(uint64_t)i, (uint64_t)attempt, frame, view};
             uint64_t r[4];
             oracle_philox4x64(ctr, key, r);
-            double u0 = unit24(r[0]), u1 = unit24(r[1]), u2 = unit24(r[2]);
+            double u0 = unit23(r[0]), u1 = unit23(r[1]), u2 = unit23(r[2]);
             double rad = sqrt(-2.0 * log(u0));
             double z0 = rad * cos(2.0 * PI * u1);
             z1 = rad * sin(2.0 * PI * u1);

@@ -57,6 +57,8 @@ class Workload:
     census_cs: bool = False
     block: tuple = (1, 1)
     median: int = 0
+    # IR sensor noise of Sec. VI-C with the D415 values, seeded by `seed`
+    noise: bool = False
 
     @property
     def nbits(self) -> int:

@@ -38,6 +38,17 @@ struct Params {
 // checking the ranges; returns a SIMSENSE status.
 int set_variant(Params& p, int opt, int value);
 
+// Sensor-noise model (Sec. VI-C) and generator seed.
+struct NoiseParams {
+    float mu = 0.0f, sigma = 0.0f, k = 1.0f, theta = 1.0f;
+    uint64_t seed = 0;
+};
+int check_noise(const NoiseParams& n);
+// Noise of one view (clean1 == nullptr) or of two views (views view0 and
+// view0 + 1) of npx pixels each; clean and noisy may be the same buffer.
+cudaError_t launch_noise(const NoiseParams& n, const uint8_t* clean0, uint8_t* noisy0, const uint8_t* clean1,
+                         uint8_t* noisy1, int npx, uint32_t frame, uint32_t view0, cudaStream_t s);
+
 // Device scratch of one handle (all owned by the handle).
 struct Scratch {
     void* codes_left = nullptr;    // H x W uint32 or uint64
@@ -127,4 +138,7 @@ struct simsense_ctx {
     ProfileRing prof;
     int device = 0;
     int last_cuda_error = 0;
+    bool noise_on = false;             // sensor noise before the census
+    simsense::NoiseParams noise;
+    uint32_t noise_frame = 0;          // frame index of the next compute call
 };

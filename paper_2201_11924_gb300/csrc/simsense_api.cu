@@ -67,9 +67,18 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
 {
     const Params& p = h->p;
     Scratch& s = h->s;
+    cudaError_t e = cudaSuccess;
+    if (h->noise_on) {
+        // sensor noise (Sec. VI-C) of both views into the staging buffers
+        // (in place when the host-buffer call staged the inputs there)
+        e = launch_noise(h->noise, left, s.stage_left, right, s.stage_right, p.W * p.H, h->noise_frame++, 0, st);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        left = s.stage_left;
+        right = s.stage_right;
+    }
     const PairPtrs pair{left, right, s.codes_left, s.codes_right, s.cost, s.paths, depth};
     const Tuning tune{};
-    cudaError_t e = mark(h, SIMSENSE_STAGE_CENSUS, false, st);
+    e = mark(h, SIMSENSE_STAGE_CENSUS, false, st);
     if (e == cudaSuccess) e = launch_census(p, &pair, 1, st);
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_CENSUS, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);
@@ -297,6 +306,39 @@ int simsense_set_option(simsense_t h, int opt, int value)
         default:
             return SIMSENSE_ERR_INVALID_ARG;
     }
+}
+
+int simsense_set_noise(simsense_t h, int enable, float mu, float sigma, float k, float theta,
+                       unsigned long long seed)
+{
+    if (!h || (enable != 0 && enable != 1)) return SIMSENSE_ERR_INVALID_ARG;
+    NoiseParams n;
+    n.mu = mu;
+    n.sigma = sigma;
+    n.k = k;
+    n.theta = theta;
+    n.seed = seed;
+    if (enable && check_noise(n) != SIMSENSE_OK) return SIMSENSE_ERR_INVALID_ARG;
+    h->noise_on = enable != 0;
+    h->noise = n;
+    h->noise_frame = 0;
+    return SIMSENSE_OK;
+}
+
+int simsense_add_noise(const uint8_t* clean, uint8_t* noisy, int W, int H, float mu, float sigma, float k,
+                       float theta, unsigned long long seed, unsigned int frame, unsigned int view,
+                       struct CUstream_st* stream)
+{
+    if (!clean || !noisy || W < 1 || H < 1 || (long long)W * H > (1ll << 30)) return SIMSENSE_ERR_INVALID_ARG;
+    NoiseParams n;
+    n.mu = mu;
+    n.sigma = sigma;
+    n.k = k;
+    n.theta = theta;
+    n.seed = seed;
+    if (check_noise(n) != SIMSENSE_OK) return SIMSENSE_ERR_INVALID_ARG;
+    cudaError_t e = launch_noise(n, clean, noisy, nullptr, nullptr, W * H, frame, view, (cudaStream_t)stream);
+    return e == cudaSuccess ? SIMSENSE_OK : SIMSENSE_ERR_CUDA;
 }
 
 int simsense_profile_read(simsense_t h, double* stage_ms, int* n_calls)

@@ -73,12 +73,38 @@ def load():
             lib.simsense_device_status.restype = ctypes.c_int
             lib.simsense_stage_name.argtypes = [I]
             lib.simsense_stage_name.restype = ctypes.c_char_p
+            U64, U32 = ctypes.c_ulonglong, ctypes.c_uint
+            lib.simsense_set_noise.argtypes = [P, I, F, F, F, F, U64]
+            lib.simsense_add_noise.argtypes = [P, P, I, I, F, F, F, F, U64, U32, U32, P]
             for fn in ("simsense_create", "simsense_compute", "simsense_compute_host",
                        "simsense_compute_debug", "simsense_set_option", "simsense_destroy",
-                       "simsense_last_cuda_error"):
+                       "simsense_last_cuda_error", "simsense_set_noise", "simsense_add_noise"):
                 getattr(lib, fn).restype = ctypes.c_int
             _lib = lib
     return _lib
+
+
+# D415 noise parameters the paper estimates (Sec. VII, sensor parameters)
+D415_NOISE = dict(mu=-0.231, sigma=0.83, k=3.98, theta=0.254)
+
+
+def add_noise(clean, noisy=None, mu=D415_NOISE["mu"], sigma=D415_NOISE["sigma"], k=D415_NOISE["k"],
+              theta=D415_NOISE["theta"], seed=0, frame=0, view=0, stream=None):
+    """IR sensor noise (Sec. VI-C) of one H x W uint8 CUDA image into noisy
+    (allocated if None; may be clean itself).  Returns noisy."""
+    import torch
+    if not isinstance(clean, torch.Tensor) or not clean.is_cuda or clean.dim() != 2:
+        raise ValueError("clean must be a 2-D CUDA tensor")
+    H, W = clean.shape
+    c = _dev_ptr(clean, torch.uint8, (H, W), "clean")
+    if noisy is None:
+        noisy = torch.empty_like(clean)
+    n = _dev_ptr(noisy, torch.uint8, (H, W), "noisy")
+    rc = load().simsense_add_noise(c, n, W, H, float(mu), float(sigma), float(k), float(theta), int(seed),
+                                   int(frame), int(view), _stream_ptr(stream))
+    if rc != 0:
+        raise SimsenseError(rc, "simsense_add_noise")
+    return noisy
 
 
 def strerror(code: int) -> str:
@@ -125,7 +151,16 @@ class SimSense:
                 wl.lr_max_diff, wl.f, wl.baseline, subpixel=wl.subpixel)
         m.set_variant(census_cs=getattr(wl, "census_cs", False), block=getattr(wl, "block", (1, 1)),
                       median=getattr(wl, "median", 0))
+        if getattr(wl, "noise", False):
+            m.set_noise(True, seed=wl.seed)
         return m
+
+    def set_noise(self, enable: bool = True, mu=D415_NOISE["mu"], sigma=D415_NOISE["sigma"],
+                  k=D415_NOISE["k"], theta=D415_NOISE["theta"], seed: int = 0):
+        """Sensor noise (Sec. VI-C) on both views of every later compute call;
+        the n-th call after this one uses frame n."""
+        self._check(load().simsense_set_noise(self.handle, int(bool(enable)), float(mu), float(sigma), float(k),
+                                              float(theta), int(seed)), "simsense_set_noise")
 
     def set_variant(self, census_cs: bool = False, block=(1, 1), median: int = 0):
         """Selects the variants of the stage (centre-symmetric census, SGBM

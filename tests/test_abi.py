@@ -72,7 +72,22 @@ def test_create_rejects_bad_arguments(lib, args):
 def test_null_handles_are_rejected(lib):
     assert lib.simsense_compute(None, None, None, None, None) == -1
     assert lib.simsense_set_option(None, 1, 0) == -1
+    assert lib.simsense_set_noise(None, 1, -0.231, 0.83, 3.98, 0.254, 1) == -1
     assert lib.simsense_destroy(None) == 0
+
+
+@pytest.mark.parametrize("W,H,k,theta,sigma", [
+    (0, 8, 3.98, 0.254, 0.83),           # empty image
+    (8, 8, 0.5, 0.254, 0.83),            # k < 1 (the rejection sampler needs k >= 1)
+    (8, 8, 3.98, 0.0, 0.83),             # theta
+    (8, 8, 3.98, 0.254, -1.0),           # sigma
+    (8, 8, float("nan"), 0.254, 0.83),
+])
+def test_add_noise_rejects_bad_arguments(lib, W, H, k, theta, sigma):
+    # argument checks come before any CUDA call: the buffers are never touched
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.simsense_add_noise(fake, fake, W, H, -0.231, sigma, k, theta, 1, 0, 0, None) == -1
+    assert lib.simsense_add_noise(None, fake, 8, 8, -0.231, 0.83, 3.98, 0.254, 1, 0, 0, None) == -1
 
 
 def test_batch_create_rejects_bad_arguments(lib):

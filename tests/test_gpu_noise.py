@@ -1,0 +1,100 @@
+"""IR sensor noise on the GPU (arxiv 2201.11924 Sec. VI-C) against the CPU
+oracle, through the C ABI.
+
+The generator (Philox4x64-10) is integer arithmetic and identical on both
+sides; the transforms run in fp32 on the GPU and fp64 in the oracle.  So
+every pixel whose decisions (the rounding of the noisy value, the
+acceptance tests of the gamma sampler) lie at least 1e-3 from their
+thresholds must match exactly; the few pixels closer than that may round the
+other way.  The stage with noise switched on must then equal the oracle run
+on the noisy images the same generator streams produce."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2201_11924_gb300 import configs, scenes
+
+pytestmark = pytest.mark.gpu
+
+P = oracle.D415_NOISE
+MARGIN = 1e-3
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2201_11924_gb300 import _build, simsense
+    _build.build()
+    return simsense
+
+
+def _gpu_noise(lib, img, seed, frame, view, **kw):
+    import torch
+    t = torch.from_numpy(img).cuda()
+    out = lib.add_noise(t, seed=seed, frame=frame, view=view, **{**P, **kw})
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape,seed,frame,view", [((217, 333), 1, 0, 0), ((64, 64), 7, 3, 1),
+                                                   ((1, 1000), 2**40 + 5, 9, 0), ((480, 640), 123, 0, 1)])
+def test_noise_matches_oracle_away_from_thresholds(lib, shape, seed, frame, view):
+    rng = np.random.default_rng(seed % 1000)
+    img = rng.integers(0, 256, shape, dtype=np.uint8)
+    g = _gpu_noise(lib, img, seed, frame, view)
+    o, _, margin = oracle.noise(img, **P, seed=seed, frame=frame, view=view)
+    sure = margin >= MARGIN
+    assert np.array_equal(g[sure], o[sure])
+    assert (~sure).mean() < 2e-3
+    assert (g != o).mean() < 1e-3
+
+
+def test_noise_in_place_and_parameter_extremes(lib):
+    import torch
+    rng = np.random.default_rng(3)
+    img = rng.integers(0, 256, (50, 70), dtype=np.uint8)
+    t = torch.from_numpy(img).cuda()
+    out = lib.add_noise(t, seed=5).cpu().numpy()
+    lib.add_noise(t, t, seed=5)                        # in place
+    assert np.array_equal(t.cpu().numpy(), out)
+    # noise-free limit: gamma -> 1, no thermal term
+    same = _gpu_noise(lib, img, 4, 0, 0, mu=0.0, sigma=0.0, k=1e8, theta=1e-8)
+    assert np.array_equal(same, img)
+    # saturation: large additive noise clamps to [0, 255]
+    sat = _gpu_noise(lib, img, 4, 0, 0, mu=0.0, sigma=500.0)
+    assert (sat == 0).any() and (sat == 255).any()
+
+
+def test_stage_with_noise_equals_oracle_on_the_noisy_pair(lib):
+    import torch
+    wl = configs.SMALL_320
+    p = scenes.make_pair(wl)
+    seed = 77
+    with lib.SimSense.from_workload(wl) as m:
+        m.set_noise(True, seed=seed)
+        L = torch.from_numpy(p["left"]).cuda()
+        R = torch.from_numpy(p["right"]).cuda()
+        for frame in range(2):                         # the n-th call uses frame n
+            d = m.compute(L, R).cpu().numpy()
+            nl = _gpu_noise(lib, p["left"], seed, frame, 0)
+            nr = _gpu_noise(lib, p["right"], seed, frame, 1)
+            o = oracle.compute(nl, nr, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq, wl.lr_max_diff,
+                               wl.subpixel, wl.f, wl.baseline)
+            valid = o["mask"] == 0
+            assert np.array_equal(d > 0, valid)
+            np.testing.assert_allclose(d[valid], o["depth"][valid], rtol=1e-5, atol=0)
+        # the host-buffer call continues the frame count (frame 2)
+        hd_t = torch.empty((wl.H, wl.W), dtype=torch.float32)
+        m.compute_host(torch.from_numpy(p["left"]), torch.from_numpy(p["right"]), hd_t)
+        torch.cuda.synchronize()
+        hd = hd_t.numpy()
+        nl = _gpu_noise(lib, p["left"], seed, 2, 0)
+        nr = _gpu_noise(lib, p["right"], seed, 2, 1)
+        o = oracle.compute(nl, nr, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq, wl.lr_max_diff,
+                           wl.subpixel, wl.f, wl.baseline)
+        valid = o["mask"] == 0
+        assert np.array_equal(hd > 0, valid)
+        m.set_noise(False)
+        plain = m.compute(L, R).cpu().numpy()
+        o0 = oracle.compute(p["left"], p["right"], wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq,
+                            wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline)
+        assert np.array_equal(plain > 0, o0["mask"] == 0)
