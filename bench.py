@@ -550,7 +550,8 @@ def main():
                          "far above the 129 MB L2", "path": "plain (one pair per call)"},
         "cells_per_s": value * wl.cells,
         "e2e": e2e,
-        "gpu_launches": 4 * args.steps,
+        # census, cost, paths, select; plus the noise, block-cost and median kernels of a variant
+        "gpu_launches": (4 + int(wl.noise) + int(wl.block != (1, 1)) + int(wl.median > 0)) * args.steps,
         "batched": batched,
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -102,11 +102,18 @@ cudaError_t cost_code(const Params& p, const PairPtrs* pairs, int n, cudaStream_
 // SGBM block cost (the variant Sec. VI-D describes: the Hamming distance
 // between the local regions of the two pixels): the per-pixel cost volume
 // `raw` averaged over the bw x bh block around each pixel (same d), over the
-// block's pixels inside the image, rounded half up, into `out`.  A thread
-// takes one 4-byte word (4 disparities) of one pixel: the block sum of each
-// byte is accumulated as two 16-bit pairs (at most 49 x 255 < 2^16), and the
-// division by the pixel count n is a multiply-high by floor(2^32 / n) + 1,
-// exact for every numerator below 2^16 and n <= 81.
+// block's pixels inside the image, rounded half up, into `out`.
+// A block takes 32 pixels of one output row: it copies the bh input row
+// segments it needs (32 + bw - 1 pixels each, all Dp bytes, 16-byte vector
+// loads; pixels outside the image as 0) into shared memory, then a thread
+// takes one 4-byte word (4 disparities) of a pixel: lanes take consecutive
+// words of one pixel, so the shared-memory reads are conflict-free.  The
+// block sum of each byte is accumulated as two 16-bit pairs (at most
+// 49 x 255 < 2^16) and divided by the in-image pixel count n with a
+// multiply-high by floor(2^32 / n) + 1, exact for every numerator below 2^16
+// and n <= 81.
+constexpr int kBlkPix = 32;
+
 struct Magic {
     uint32_t m[82];
 };
@@ -115,32 +122,43 @@ template <int N>
 __global__ void __launch_bounds__(256)
 block_cost_kernel(PairTable<N> pt, int W, int H, int Dp, int bw, int bh, Magic mg)
 {
-    const int words = Dp >> 2;                         // words per pixel
-    const int ppb = 256 / words;                       // pixels per block
-    if (threadIdx.x >= ppb * words) return;          // Dp = 192: 5 pixels x 48 words
-    const int x = blockIdx.x * ppb + threadIdx.x / words;
-    const int w = threadIdx.x % words;
-    const int y = blockIdx.y;
-    if (x >= W) return;
-    const uint32_t* __restrict__ raw = reinterpret_cast<const uint32_t*>(pt.p[blockIdx.z].vol);
+    extern __shared__ __align__(16) uint8_t seg[];     // bh x (kBlkPix + bw - 1) x Dp
+    const uint8_t* __restrict__ raw = pt.p[blockIdx.z].vol;
     uint32_t* __restrict__ out = reinterpret_cast<uint32_t*>(pt.p[blockIdx.z].cost);
+    const int y = blockIdx.y, x0 = blockIdx.x * kBlkPix;
     const int rx = bw >> 1, ry = bh >> 1;
-    const int x0 = max(x - rx, 0), x1 = min(x + rx, W - 1);
-    const int y0 = max(y - ry, 0), y1 = min(y + ry, H - 1);
-    uint32_t ev = 0, od = 0;                           // (b0, b2) and (b1, b3) sums
-    for (int yy = y0; yy <= y1; yy++) {
-        const uint32_t* row = raw + ((size_t)yy * W) * words + w;
-        for (int xx = x0; xx <= x1; xx++) {
-            const uint32_t v = __ldg(row + (size_t)xx * words);
-            ev += v & 0x00ff00ffu;
-            od += (v >> 8) & 0x00ff00ffu;
-        }
+    const int span = kBlkPix + bw - 1;                 // pixels per staged row
+    const int vec = Dp >> 4;                           // 16-byte vectors per pixel
+    for (int i = threadIdx.x; i < bh * span * vec; i += blockDim.x) {
+        const int v = i % vec, px = (i / vec) % span, r = i / (vec * span);
+        const int xx = x0 - rx + px, yy = y - ry + r;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (xx >= 0 && xx < W && yy >= 0 && yy < H)
+            val = __ldg(reinterpret_cast<const uint4*>(raw + ((size_t)yy * W + xx) * Dp) + v);
+        reinterpret_cast<uint4*>(seg)[(r * span + px) * vec + v] = val;
     }
-    const uint32_t n = (uint32_t)((x1 - x0 + 1) * (y1 - y0 + 1));
-    const uint32_t m = mg.m[n], h = n >> 1;
-    const uint32_t c0 = __umulhi((ev & 0xffffu) + h, m), c2 = __umulhi((ev >> 16) + h, m);
-    const uint32_t c1 = __umulhi((od & 0xffffu) + h, m), c3 = __umulhi((od >> 16) + h, m);
-    out[((size_t)y * W + x) * words + w] = c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
+    __syncthreads();
+    const int words = Dp >> 2;
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(seg);
+    const int ylo = max(y - ry, 0), yhi = min(y + ry, H - 1);
+    for (int i = threadIdx.x; i < kBlkPix * words; i += blockDim.x) {
+        const int w = i % words, px = i / words;
+        const int x = x0 + px;
+        if (x >= W) break;                             // i grows with px
+        uint32_t ev = 0, od = 0;                       // (b0, b2) and (b1, b3) sums
+        for (int r = 0; r < bh; r++)
+            for (int u = 0; u < bw; u++) {
+                const uint32_t v = s32[(r * span + px + u) * words + w];
+                ev += v & 0x00ff00ffu;
+                od += (v >> 8) & 0x00ff00ffu;
+            }
+        const int xlo = max(x - rx, 0), xhi = min(x + rx, W - 1);
+        const uint32_t n = (uint32_t)((xhi - xlo + 1) * (yhi - ylo + 1));
+        const uint32_t m = mg.m[n], h = n >> 1;
+        const uint32_t c0 = __umulhi((ev & 0xffffu) + h, m), c2 = __umulhi((ev >> 16) + h, m);
+        const uint32_t c1 = __umulhi((od & 0xffffu) + h, m), c3 = __umulhi((od >> 16) + h, m);
+        out[((size_t)y * W + x) * words + w] = c0 | (c1 << 8) | (c2 << 16) | (c3 << 24);
+    }
 }
 
 template <int N>
@@ -150,9 +168,12 @@ cudaError_t block_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStrea
     for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
     Magic mg{};
     for (uint32_t k = 1; k < 82; k++) mg.m[k] = (uint32_t)(0x100000000ull / k) + 1u;
-    const int ppb = 256 / (p.Dp / 4);
-    dim3 grid((p.W + ppb - 1) / ppb, p.H, n);
-    block_cost_kernel<N><<<grid, 256, 0, s>>>(pt, p.W, p.H, p.Dp, p.block_w, p.block_h, mg);
+    const size_t smem = (size_t)p.block_h * (kBlkPix + p.block_w - 1) * p.Dp;
+    auto kernel = block_cost_kernel<N>;
+    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.W + kBlkPix - 1) / kBlkPix, p.H, n);
+    kernel<<<grid, 256, smem, s>>>(pt, p.W, p.H, p.Dp, p.block_w, p.block_h, mg);
     return cudaGetLastError();
 }
 
