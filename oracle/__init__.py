@@ -37,7 +37,9 @@ def build(force: bool = False) -> str:
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    # -ffp-contract=off: no fused multiply-adds, so the fp64 camera arithmetic
+    # rounds after every operation as written
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -69,6 +71,10 @@ def _load():
             lib.oracle_philox4x64.argtypes = [P, P, P]
             lib.oracle_philox4x64.restype = None
             lib.oracle_noise.argtypes = [P, I, I, Dd, Dd, Dd, Dd, U64, U32, U32, P, P, P]
+            lib.oracle_rectify.argtypes = [P, I, I, P, P]
+            lib.oracle_register.argtypes = [P, I, I, Dd, Dd, Dd, Dd, P, P, I, I]
+            lib.oracle_rectify.restype = ctypes.c_int
+            lib.oracle_register.restype = ctypes.c_int
             for fn in ("oracle_census", "oracle_cost", "oracle_path", "oracle_aggregate",
                        "oracle_select", "oracle_compute", "oracle_census_cs", "oracle_cost_block",
                        "oracle_median", "oracle_compute_ex", "oracle_noise"):
@@ -192,6 +198,38 @@ def noise(clean, mu, sigma, k, theta, seed, frame=0, view=0):
                                 int(seed), int(frame), int(view), _ptr(value), _ptr(noisy), _ptr(margin)),
            "noise")
     return noisy, value, margin
+
+
+def camera(fx, fy, cx, cy, k1=0.0, k2=0.0, p1=0.0, p2=0.0, k3=0.0, R=None, rfx=None, rfy=None, rcx=None,
+           rcy=None) -> np.ndarray:
+    """Raw and rectified camera of one view as the 22 doubles the oracle takes
+    (rectified intrinsics default to the raw ones, R to the identity)."""
+    R = np.eye(3) if R is None else np.asarray(R, dtype=np.float64)
+    return np.array([fx, fy, cx, cy, k1, k2, p1, p2, k3, *R.ravel(),
+                     fx if rfx is None else rfx, fy if rfy is None else rfy,
+                     cx if rcx is None else rcx, cy if rcy is None else rcy], dtype=np.float64)
+
+
+def rectify(raw, cam) -> np.ndarray:
+    """Rectified view (uint8, same size) of a raw view under `camera(...)`."""
+    raw = np.ascontiguousarray(raw, dtype=np.uint8)
+    H, W = raw.shape
+    c = np.ascontiguousarray(cam, dtype=np.float64)
+    out = np.empty((H, W), dtype=np.uint8)
+    _check(_load().oracle_rectify(_ptr(raw), W, H, _ptr(c), _ptr(out)), "rectify")
+    return out
+
+
+def register(depth, fx, fy, cx, cy, fx2, fy2, cx2, cy2, R, t, W2, H2) -> np.ndarray:
+    """Depth (float32, W x H, 0 invalid) of camera (fx, fy, cx, cy) splatted
+    into an RGB camera (fx2, fy2, cx2, cy2) at pose (R, t), W2 x H2."""
+    depth = np.ascontiguousarray(depth, dtype=np.float32)
+    H, W = depth.shape
+    reg = np.array([fx2, fy2, cx2, cy2, *np.asarray(R, dtype=np.float64).ravel(), *t], dtype=np.float64)
+    out = np.empty((H2, W2), dtype=np.float32)
+    _check(_load().oracle_register(_ptr(depth), W, H, float(fx), float(fy), float(cx), float(cy), _ptr(reg),
+                                   _ptr(out), W2, H2), "register")
+    return out
 
 
 def compute(left, right, D, ww, wh, P1, P2, paths, uniq, lr_max_diff, subpixel, f, baseline,

@@ -54,6 +54,26 @@
  *  rejection method (k >= 1), at most 16 attempts (if all are rejected,
  *  gamma = (k - 1/3) theta).
  *
+ * Rectification and depth registration (Sec. VI-D: the stage "first
+ *  performs a stereo rectification" and ends with "an optional depth
+ *  registration that aligns the depth map to the RGB camera frame"; the paper
+ *  gives no camera model).  Readings:
+ *  - rectification: for rectified pixel (u, v), the ray R^T ((u - rcx)/rfx,
+ *    (v - rcy)/rfy, 1) in the raw camera, normalised by its z, distorted by
+ *    the Brown-Conrady model (k1, k2, k3 radial, p1, p2 tangential) and
+ *    projected with (fx, fy, cx, cy) gives the raw position (ur, vr), all in
+ *    fp64 with + - * / only.  Fixed point: x0 = floor(ur), ax = the fraction
+ *    times 256 rounded half to even (256 carries into x0 + 1), the same for
+ *    y; the value is the 8-bit bilinear mix ((256-ax)(256-ay) I00 + ...
+ *    + 32768) >> 16, taps outside the raw image reading 0.  A ray with
+ *    z <= 0 gives 0.
+ *  - registration: a valid depth pixel (u, v, Z) of the rectified left
+ *    camera (fx, fy, cx, cy) is back-projected, moved by the rigid transform
+ *    (R, t) into the RGB camera, projected with its intrinsics and splatted
+ *    to the nearest RGB pixel (floor(u' + 1/2)), keeping the smallest Z' > 0
+ *    there (a z-buffer); fp64 with + - * / only, Z' rounded to fp32; RGB
+ *    pixels no depth pixel reaches stay 0.
+ *
  * Variants Sec. VI-D also names (optional in the stage):
  *  - centre-symmetric census (CSCT): for every offset o of the window that
  *    precedes the centre in raster order, bit = [I(p+o) < I(p-o)]; a pair
@@ -429,6 +449,98 @@ int oracle_noise(const uint8_t* clean, int W, int H, double mu, double sigma, do
         if (value) value[i] = val;
         if (margin) margin[i] = m;
     }
+    return ORACLE_OK;
+}
+
+/* -------------------------------------------- rectification, registration */
+
+/* Camera of one raw view and its rectified counterpart. */
+typedef struct {
+    double fx, fy, cx, cy;        /* raw intrinsics */
+    double k1, k2, p1, p2, k3;    /* Brown-Conrady distortion */
+    double R[9];                  /* rectified ray = R * raw ray, row-major */
+    double rfx, rfy, rcx, rcy;    /* rectified intrinsics */
+} oracle_camera;
+
+/* Fixed-point source position of rectified pixel (u, v): x0, y0 and the
+ * 1/256 fractions ax, ay; returns 0 when the ray points behind the camera. */
+static int rect_source(const oracle_camera* c, int u, int v, int* x0, int* y0, int* ax, int* ay)
+{
+    double xr = ((double)u - c->rcx) / c->rfx;
+    double yr = ((double)v - c->rcy) / c->rfy;
+    /* raw ray = R^T (xr, yr, 1) */
+    double X = c->R[0] * xr + c->R[3] * yr + c->R[6];
+    double Y = c->R[1] * xr + c->R[4] * yr + c->R[7];
+    double Z = c->R[2] * xr + c->R[5] * yr + c->R[8];
+    if (!(Z > 0.0)) return 0;
+    double x = X / Z, y = Y / Z;
+    double r2 = x * x + y * y;
+    double radial = 1.0 + c->k1 * r2 + c->k2 * r2 * r2 + c->k3 * r2 * r2 * r2;
+    double xd = x * radial + 2.0 * c->p1 * x * y + c->p2 * (r2 + 2.0 * x * x);
+    double yd = y * radial + c->p1 * (r2 + 2.0 * y * y) + 2.0 * c->p2 * x * y;
+    double ur = c->fx * xd + c->cx, vr = c->fy * yd + c->cy;
+    if (!(fabs(ur) < 1e9) || !(fabs(vr) < 1e9)) return 0;
+    double fxl = floor(ur), fyl = floor(vr);
+    int a = (int)nearbyint((ur - fxl) * 256.0), b = (int)nearbyint((vr - fyl) * 256.0);
+    int xi = (int)fxl, yi = (int)fyl;
+    if (a == 256) { a = 0; xi++; }
+    if (b == 256) { b = 0; yi++; }
+    *x0 = xi; *y0 = yi; *ax = a; *ay = b;
+    return 1;
+}
+
+/* Rectification of one view (raw and rectified images both W x H bytes). */
+int oracle_rectify(const uint8_t* raw, int W, int H, const double* cam, uint8_t* out)
+{
+    if (!raw || !out || !cam || W <= 0 || H <= 0) return ORACLE_BAD_ARG;
+    oracle_camera c;
+    memcpy(&c, cam, sizeof(c));
+    for (int v = 0; v < H; v++)
+        for (int u = 0; u < W; u++) {
+            int x0, y0, ax, ay;
+            uint32_t val = 0;
+            if (rect_source(&c, u, v, &x0, &y0, &ax, &ay)) {
+                uint32_t t[4] = {0, 0, 0, 0};   /* taps (x0,y0) (x0+1,y0) (x0,y0+1) (x0+1,y0+1) */
+                for (int k = 0; k < 4; k++) {
+                    int xx = x0 + (k & 1), yy = y0 + (k >> 1);
+                    if (xx >= 0 && xx < W && yy >= 0 && yy < H) t[k] = raw[yy * W + xx];
+                }
+                uint32_t bx = 256 - (uint32_t)ax, by = 256 - (uint32_t)ay;
+                val = (bx * by * t[0] + (uint32_t)ax * by * t[1] + bx * (uint32_t)ay * t[2] +
+                       (uint32_t)ax * (uint32_t)ay * t[3] + 32768u) >> 16;
+            }
+            out[v * W + u] = (uint8_t)val;
+        }
+    return ORACLE_OK;
+}
+
+/* Registration of a depth map (W x H, 0 = invalid) of the camera
+ * (fx, fy, cx, cy) into an RGB camera: reg = {fx2, fy2, cx2, cy2, R[9], t[3]}.
+ * out: W2 x H2 floats. */
+int oracle_register(const float* depth, int W, int H, double fx, double fy, double cx, double cy,
+                    const double* reg, float* out, int W2, int H2)
+{
+    if (!depth || !reg || !out || W <= 0 || H <= 0 || W2 <= 0 || H2 <= 0) return ORACLE_BAD_ARG;
+    const double fx2 = reg[0], fy2 = reg[1], cx2 = reg[2], cy2 = reg[3];
+    const double* R = reg + 4;
+    const double* t = reg + 13;
+    for (int i = 0; i < W2 * H2; i++) out[i] = 0.0f;
+    for (int v = 0; v < H; v++)
+        for (int u = 0; u < W; u++) {
+            double Z = depth[v * W + u];
+            if (!(Z > 0.0)) continue;
+            double X = ((double)u - cx) / fx * Z, Y = ((double)v - cy) / fy * Z;
+            double X2 = R[0] * X + R[1] * Y + R[2] * Z + t[0];
+            double Y2 = R[3] * X + R[4] * Y + R[5] * Z + t[1];
+            double Z2 = R[6] * X + R[7] * Y + R[8] * Z + t[2];
+            if (!(Z2 > 0.0)) continue;
+            double u2 = fx2 * (X2 / Z2) + cx2, v2 = fy2 * (Y2 / Z2) + cy2;
+            double pu = floor(u2 + 0.5), pv = floor(v2 + 0.5);
+            if (!(pu >= 0.0 && pu < (double)W2 && pv >= 0.0 && pv < (double)H2)) continue;
+            int k = (int)pv * W2 + (int)pu;
+            float z = (float)Z2;
+            if (out[k] == 0.0f || z < out[k]) out[k] = z;
+        }
     return ORACLE_OK;
 }
 

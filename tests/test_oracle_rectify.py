@@ -1,0 +1,112 @@
+"""Pins of the oracle's rectification and depth registration (arxiv
+2201.11924 Sec. VI-D names both; the camera model is a reading: pinhole with
+Brown-Conrady distortion, fixed-point bilinear resampling, nearest-pixel
+z-buffered splatting).
+
+The pins are exact geometric cases (identity, integer shifts, a quarter turn,
+a half-pixel shift against a library bilinear interpolation), the distortion
+polynomial at points where it is known in closed form, and the z-buffer and
+coverage properties of the registration."""
+import numpy as np
+import pytest
+import scipy.ndimage
+
+import oracle
+
+
+def _img(H=40, W=48, seed=1):
+    return np.random.default_rng(seed).integers(0, 256, (H, W), dtype=np.uint8)
+
+
+def test_identity_camera_returns_the_image():
+    img = _img()
+    cam = oracle.camera(300.0, 300.0, 23.5, 19.5)
+    assert np.array_equal(oracle.rectify(img, cam), img)
+
+
+@pytest.mark.parametrize("dx,dy", [(3, 0), (0, -2), (-5, 4)])
+def test_principal_point_shift_is_an_integer_translation(dx, dy):
+    # rectified cx' = cx + dx maps rectified u to raw u - dx
+    img = _img(seed=100 + dx * 10 + dy)
+    H, W = img.shape
+    cam = oracle.camera(250.0, 250.0, 20.0, 18.0, rcx=20.0 + dx, rcy=18.0 + dy)
+    out = oracle.rectify(img, cam)
+    want = np.zeros_like(img)
+    ys, xs = np.mgrid[0:H, 0:W]
+    sx, sy = xs - dx, ys - dy
+    ok = (sx >= 0) & (sx < W) & (sy >= 0) & (sy < H)
+    want[ok] = img[sy[ok], sx[ok]]
+    assert np.array_equal(out, want)
+
+
+def test_quarter_turn_about_the_axis_rotates_the_image():
+    img = _img(32, 32, seed=4)
+    c = 15.5                                   # centre of a 32 x 32 image
+    R = [[0, -1, 0], [1, 0, 0], [0, 0, 1]]     # rectified ray = R raw ray
+    out = oracle.rectify(img, oracle.camera(100.0, 100.0, c, c, R=R))
+    # raw ray = R^T rectified ray = (yr, -xr, 1): out[v, u] = img[2c - u, v],
+    # the image turned a quarter clockwise
+    assert np.array_equal(out, np.rot90(img, k=-1))
+
+
+def test_half_pixel_shift_matches_library_bilinear():
+    img = _img(seed=7)
+    H, W = img.shape
+    cam = oracle.camera(200.0, 200.0, 22.0, 17.0, rcx=22.5, rcy=17.25)
+    out = oracle.rectify(img, cam).astype(int)
+    ys, xs = np.mgrid[0:H, 0:W].astype(float)
+    ref = scipy.ndimage.map_coordinates(img.astype(float), [ys - 0.25, xs - 0.5], order=1, mode="constant", cval=0)
+    inner = (slice(1, H - 1), slice(1, W - 1))
+    assert np.abs(out[inner] - ref[inner]).max() <= 0.5 + 1e-9   # the fixed point holds 1/256 steps
+
+
+def test_radial_distortion_moves_points_by_the_polynomial():
+    # on the x axis y = 0: x_d = x (1 + k1 x^2 + k2 x^4 + k3 x^6); a raw image
+    # that is a ramp in x (value = raw column) reads back the distorted column
+    W, H = 64, 9
+    ramp = np.tile(np.arange(W, dtype=np.uint8), (H, 1))
+    f, cx, cy = 40.0, 10.0, 4.0
+    k1, k2, k3 = 0.02, -0.001, 0.0001
+    out = oracle.rectify(ramp, oracle.camera(f, f, cx, cy, k1=k1, k2=k2, k3=k3))
+    for u in (10, 15, 20, 25, 30):
+        x = (u - cx) / f
+        ur = f * x * (1 + k1 * x * x + k2 * x ** 4 + k3 * x ** 6) + cx
+        assert abs(int(out[4, u]) - ur) <= 0.5 + 1.0 / 256, u
+
+
+def test_tangential_terms_are_symmetric_in_their_axes():
+    # p1 alone shifts v on the y axis as p1 (3 y^2); p2 alone shifts u on the x axis as p2 (3 x^2)
+    W, H = 40, 40
+    rampx = np.tile(np.arange(W, dtype=np.uint8), (H, 1))
+    f, c, p = 30.0, 8.0, 0.01
+    out = oracle.rectify(rampx, oracle.camera(f, f, c, c, p2=p))
+    for u in (12, 18, 24):
+        x = (u - c) / f
+        assert abs(int(out[int(c), u]) - (f * (x + p * 3 * x * x) + c)) <= 0.5 + 1.0 / 256
+
+
+def test_registration_identity_and_zbuffer():
+    rng = np.random.default_rng(2)
+    depth = rng.uniform(0.4, 2.0, (30, 40)).astype(np.float32)
+    depth[rng.random(depth.shape) < 0.2] = 0.0
+    f, cx, cy = 100.0, 19.5, 14.5
+    same = oracle.register(depth, f, f, cx, cy, f, f, cx, cy, np.eye(3), [0, 0, 0], 40, 30)
+    assert np.array_equal(same, depth)
+    # a camera half the focal length: 2x2 depth blocks land on one pixel, the nearest wins
+    half = oracle.register(depth, f, f, cx, cy, f / 2, f / 2, cx / 2 - 0.25, cy / 2 - 0.25, np.eye(3), [0, 0, 0], 20, 15)
+    blocks = np.where(depth > 0, depth, np.inf).reshape(15, 2, 20, 2).min(axis=(1, 3))
+    want = np.where(np.isfinite(blocks), blocks, 0).astype(np.float32)
+    assert np.array_equal(half, want)
+
+
+def test_registration_translation_along_the_axis():
+    # a fronto-parallel plane at Z moved by tz: every pixel keeps its ray
+    # direction scaled by Z / (Z + tz) about the principal point, depth Z + tz
+    depth = np.full((21, 31), 1.5, dtype=np.float32)
+    f, cx, cy, tz = 80.0, 15.0, 10.0, 1.5
+    out = oracle.register(depth, f, f, cx, cy, f, f, cx, cy, np.eye(3), [0, 0, tz], 31, 21)
+    filled = out > 0
+    assert np.allclose(out[filled], 3.0)
+    # the plane shrinks by half about the principal point: columns 8..22 only
+    cols = np.flatnonzero(filled.any(axis=0))
+    assert cols.min() >= 7 and cols.max() <= 23 and filled.sum() == len(np.unique(np.floor((np.arange(31) - cx) / 2 + cx + 0.5))) * len(np.unique(np.floor((np.arange(21) - cy) / 2 + cy + 0.5)))
