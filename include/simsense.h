@@ -237,6 +237,64 @@ int simsense_add_noise(const uint8_t* clean, uint8_t* noisy, int W, int H, float
                        float theta, unsigned long long seed, unsigned int frame, unsigned int view,
                        struct CUstream_st* stream);
 
+/*
+ * Stereo rectification and depth registration (arxiv 2201.11924 Sec. VI-D:
+ * the stage "first performs a stereo rectification to project the images onto
+ * a common image plane" and ends with "an optional depth registration that
+ * aligns the depth map to the RGB camera frame").  The paper gives no camera
+ * model; the library's reading:
+ *  - camera of one view: raw intrinsics (fx, fy, cx, cy) in pixels, Brown-
+ *    Conrady distortion (k1, k2, k3 radial, p1, p2 tangential), rectifying
+ *    rotation R (row-major; rectified ray = R * raw ray) and rectified
+ *    intrinsics (rfx, rfy, rcx, rcy).  Rectified pixel (u, v) samples the raw
+ *    image at (fx x_d + cx, fy y_d + cy), where (x, y) is the raw ray
+ *    R^T ((u - rcx)/rfx, (v - rcy)/rfy, 1) divided by its z and
+ *    x_d = x (1 + k1 r^2 + k2 r^4 + k3 r^6) + 2 p1 x y + p2 (r^2 + 2 x^2),
+ *    y_d = y (1 + k1 r^2 + k2 r^4 + k3 r^6) + p1 (r^2 + 2 y^2) + 2 p2 x y;
+ *    computed in fp64 without fused multiply-adds, quantised to 1/256 px
+ *    (half to even) and resampled by 8-bit fixed-point bilinear
+ *    interpolation; taps outside the raw image read 0, rays with z <= 0 give 0.
+ *    Raw and rectified images have the same size W x H.
+ *  - registration: every depth pixel (u, v) with Z > 0 of the camera
+ *    (fx, fy, cx, cy) goes to X = (u - cx)/fx Z, Y = (v - cy)/fy Z, then
+ *    P' = R (X, Y, Z) + t in the RGB camera (fx2, fy2, cx2, cy2), which
+ *    projects it to the nearest pixel floor(fx2 X'/Z' + cx2 + 1/2), ...;
+ *    each RGB pixel keeps the smallest Z' > 0 (fp32), others are 0.
+ *
+ * simsense_set_rectify: rectify both raw views (after the sensor noise,
+ * before the census) in every later compute call of h; NULL, NULL switches
+ * it off.  Computes the two per-pixel maps once (8 bytes per pixel each,
+ * allocated here, freed by simsense_destroy or the next call).  Returns
+ * SIMSENSE_ERR_INVALID_ARG for one NULL camera or a non-finite or zero focal
+ * length, SIMSENSE_ERR_OOM, SIMSENSE_ERR_CUDA.
+ * simsense_rectify: one view, map and resampling in one launch; raw and out
+ * are W x H device bytes (not the same buffer).
+ * simsense_register_depth: depth is W x H device floats (0 = invalid), out is
+ * reg->W2 x reg->H2 device floats, cleared here.  Both asynchronous on
+ * stream; SIMSENSE_ERR_INVALID_ARG for NULL pointers, sizes outside
+ * 1..32000 or non-finite parameters.
+ */
+typedef struct {
+    double fx, fy, cx, cy;
+    double k1, k2, p1, p2, k3;
+    double R[9];
+    double rfx, rfy, rcx, rcy;
+} simsense_camera_t;
+
+typedef struct {
+    double fx, fy, cx, cy;        /* the depth map's camera */
+    double fx2, fy2, cx2, cy2;    /* the RGB camera */
+    double R[9];                  /* depth camera -> RGB camera, row-major */
+    double t[3];                  /* metres */
+    int W2, H2;                   /* RGB image size */
+} simsense_registration_t;
+
+int simsense_set_rectify(simsense_t h, const simsense_camera_t* left, const simsense_camera_t* right);
+int simsense_rectify(const uint8_t* raw, uint8_t* out, int W, int H, const simsense_camera_t* cam,
+                     struct CUstream_st* stream);
+int simsense_register_depth(const float* depth, int W, int H, const simsense_registration_t* reg, float* out,
+                            struct CUstream_st* stream);
+
 /* Set an option (SIMSENSE_OPT_*).  Takes effect at the next compute call. */
 int simsense_set_option(simsense_t h, int opt, int value);
 

@@ -38,6 +38,13 @@ struct Params {
 // checking the ranges; returns a SIMSENSE status.
 int set_variant(Params& p, int opt, int value);
 
+// Rectification (Sec. VI-D): checks a camera, computes a view's per-pixel
+// map (x0, y0, ax, ay) and resamples both views through their maps.
+int check_camera(const simsense_camera_t& c);
+cudaError_t launch_rect_map(const simsense_camera_t& c, int W, int H, short4* map, cudaStream_t s);
+cudaError_t launch_remap(const uint8_t* raw0, const short4* map0, uint8_t* out0, const uint8_t* raw1,
+                         const short4* map1, uint8_t* out1, int W, int H, cudaStream_t s);
+
 // Sensor-noise model (Sec. VI-C) and generator seed.
 struct NoiseParams {
     float mu = 0.0f, sigma = 0.0f, k = 1.0f, theta = 1.0f;
@@ -141,4 +148,6 @@ struct simsense_ctx {
     bool noise_on = false;             // sensor noise before the census
     simsense::NoiseParams noise;
     uint32_t noise_frame = 0;          // frame index of the next compute call
+    short4* rect_map[2] = {nullptr, nullptr};    // rectification maps (both or none)
+    uint8_t* rect_img[2] = {nullptr, nullptr};   // rectified views
 };

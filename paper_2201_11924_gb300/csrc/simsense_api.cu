@@ -76,6 +76,13 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
         left = s.stage_left;
         right = s.stage_right;
     }
+    if (h->rect_map[0]) {
+        // rectification (Sec. VI-D) of both views through their maps
+        e = launch_remap(left, h->rect_map[0], h->rect_img[0], right, h->rect_map[1], h->rect_img[1], p.W, p.H, st);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+        left = h->rect_img[0];
+        right = h->rect_img[1];
+    }
     const PairPtrs pair{left, right, s.codes_left, s.codes_right, s.cost, s.paths, depth};
     const Tuning tune{};
     e = mark(h, SIMSENSE_STAGE_CENSUS, false, st);
@@ -308,6 +315,50 @@ int simsense_set_option(simsense_t h, int opt, int value)
     }
 }
 
+namespace {
+
+void free_rectify(simsense_ctx* h)
+{
+    for (int v = 0; v < 2; v++) {
+        cudaFree(h->rect_map[v]);
+        cudaFree(h->rect_img[v]);
+        h->rect_map[v] = nullptr;
+        h->rect_img[v] = nullptr;
+    }
+}
+
+}  // namespace
+
+int simsense_set_rectify(simsense_t h, const simsense_camera_t* left, const simsense_camera_t* right)
+{
+    if (!h || (!left) != (!right)) return SIMSENSE_ERR_INVALID_ARG;
+    if (left && (check_camera(*left) != SIMSENSE_OK || check_camera(*right) != SIMSENSE_OK))
+        return SIMSENSE_ERR_INVALID_ARG;
+    DeviceGuard g(h->device);
+    if (!g.ok) return cuda_fail(h, cudaGetLastError());
+    cudaError_t e = cudaDeviceSynchronize();       // no earlier call still reads the old maps
+    if (e != cudaSuccess) return cuda_fail(h, e);
+    free_rectify(h);
+    if (!left) return SIMSENSE_OK;
+    const size_t npx = (size_t)h->p.W * h->p.H;
+    for (int v = 0; v < 2; v++) {
+        if (cudaMalloc((void**)&h->rect_map[v], npx * sizeof(short4)) != cudaSuccess ||
+            cudaMalloc((void**)&h->rect_img[v], npx) != cudaSuccess) {
+            cudaGetLastError();
+            free_rectify(h);
+            return SIMSENSE_ERR_OOM;
+        }
+    }
+    e = launch_rect_map(*left, h->p.W, h->p.H, h->rect_map[0], nullptr);
+    if (e == cudaSuccess) e = launch_rect_map(*right, h->p.W, h->p.H, h->rect_map[1], nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_rectify(h);
+        return cuda_fail(h, e);
+    }
+    return SIMSENSE_OK;
+}
+
 int simsense_set_noise(simsense_t h, int enable, float mu, float sigma, float k, float theta,
                        unsigned long long seed)
 {
@@ -401,6 +452,7 @@ int simsense_destroy(simsense_t h)
     DeviceGuard g(h->device);
     free_scratch(h->s);
     free_profile(h->prof);
+    free_rectify(h);
     delete h;
     return SIMSENSE_OK;
 }

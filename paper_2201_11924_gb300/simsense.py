@@ -46,6 +46,33 @@ class DebugT(ctypes.Structure):
                 ("disparity", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
 
 
+class CameraT(ctypes.Structure):
+    """simsense_camera_t: raw intrinsics, Brown-Conrady distortion, rectifying
+    rotation (row-major) and rectified intrinsics."""
+    _fields_ = [(n, ctypes.c_double) for n in ("fx", "fy", "cx", "cy", "k1", "k2", "p1", "p2", "k3")] + \
+               [("R", ctypes.c_double * 9)] + [(n, ctypes.c_double) for n in ("rfx", "rfy", "rcx", "rcy")]
+
+
+class RegistrationT(ctypes.Structure):
+    """simsense_registration_t: depth camera, RGB camera, pose and RGB size."""
+    _fields_ = [(n, ctypes.c_double) for n in ("fx", "fy", "cx", "cy", "fx2", "fy2", "cx2", "cy2")] + \
+               [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3), ("W2", ctypes.c_int), ("H2", ctypes.c_int)]
+
+
+def camera_t(values) -> CameraT:
+    """A camera from the 22 numbers fx fy cx cy k1 k2 p1 p2 k3 R[9] rfx rfy rcx rcy."""
+    v = [float(x) for x in values]
+    if len(v) != 22:
+        raise ValueError("a camera has 22 numbers")
+    return CameraT(*v[:9], (ctypes.c_double * 9)(*v[9:18]), *v[18:])
+
+
+def registration_t(fx, fy, cx, cy, fx2, fy2, cx2, cy2, R, t, W2, H2) -> RegistrationT:
+    R = [float(x) for row in R for x in (row if hasattr(row, "__len__") else [row])]
+    return RegistrationT(float(fx), float(fy), float(cx), float(cy), float(fx2), float(fy2), float(cx2), float(cy2),
+                         (ctypes.c_double * 9)(*R), (ctypes.c_double * 3)(*[float(x) for x in t]), int(W2), int(H2))
+
+
 def load():
     """Load libsimsense.so (raises if it has not been built)."""
     global _lib
@@ -74,6 +101,11 @@ def load():
             lib.simsense_stage_name.argtypes = [I]
             lib.simsense_stage_name.restype = ctypes.c_char_p
             U64, U32 = ctypes.c_ulonglong, ctypes.c_uint
+            lib.simsense_set_rectify.argtypes = [P, ctypes.POINTER(CameraT), ctypes.POINTER(CameraT)]
+            lib.simsense_rectify.argtypes = [P, P, I, I, ctypes.POINTER(CameraT), P]
+            lib.simsense_register_depth.argtypes = [P, I, I, ctypes.POINTER(RegistrationT), P, P]
+            for fn in ("simsense_set_rectify", "simsense_rectify", "simsense_register_depth"):
+                getattr(lib, fn).restype = ctypes.c_int
             lib.simsense_set_noise.argtypes = [P, I, F, F, F, F, U64]
             lib.simsense_add_noise.argtypes = [P, P, I, I, F, F, F, F, U64, U32, U32, P]
             for fn in ("simsense_create", "simsense_compute", "simsense_compute_host",
@@ -105,6 +137,36 @@ def add_noise(clean, noisy=None, mu=D415_NOISE["mu"], sigma=D415_NOISE["sigma"],
     if rc != 0:
         raise SimsenseError(rc, "simsense_add_noise")
     return noisy
+
+
+def rectify(raw, cam, out=None, stream=None):
+    """Rectified view (Sec. VI-D) of an H x W uint8 CUDA image; cam = 22
+    numbers (see camera_t)."""
+    import torch
+    H, W = raw.shape
+    r = _dev_ptr(raw, torch.uint8, (H, W), "raw")
+    if out is None:
+        out = torch.empty_like(raw)
+    o = _dev_ptr(out, torch.uint8, (H, W), "out")
+    c = camera_t(cam)
+    rc = load().simsense_rectify(r, o, W, H, ctypes.byref(c), _stream_ptr(stream))
+    if rc != 0:
+        raise SimsenseError(rc, "simsense_rectify")
+    return out
+
+
+def register_depth(depth, reg: "RegistrationT", stream=None):
+    """Depth map (H x W float32 CUDA, 0 invalid) splatted into an RGB camera
+    (Sec. VI-D); returns the reg.H2 x reg.W2 map."""
+    import torch
+    H, W = depth.shape
+    d = _dev_ptr(depth, torch.float32, (H, W), "depth")
+    out = torch.empty((reg.H2, reg.W2), dtype=torch.float32, device=depth.device)
+    rc = load().simsense_register_depth(d, W, H, ctypes.byref(reg), ctypes.c_void_p(out.data_ptr()),
+                                        _stream_ptr(stream))
+    if rc != 0:
+        raise SimsenseError(rc, "simsense_register_depth")
+    return out
 
 
 def strerror(code: int) -> str:
@@ -161,6 +223,16 @@ class SimSense:
         the n-th call after this one uses frame n."""
         self._check(load().simsense_set_noise(self.handle, int(bool(enable)), float(mu), float(sigma), float(k),
                                               float(theta), int(seed)), "simsense_set_noise")
+
+    def set_rectify(self, left_cam=None, right_cam=None):
+        """Rectify both raw views before the census (22-number cameras, see
+        camera_t); no arguments switch it off."""
+        if left_cam is None:
+            rc = load().simsense_set_rectify(self.handle, None, None)
+        else:
+            lc, rc_ = camera_t(left_cam), camera_t(right_cam)
+            rc = load().simsense_set_rectify(self.handle, ctypes.byref(lc), ctypes.byref(rc_))
+        self._check(rc, "simsense_set_rectify")
 
     def set_variant(self, census_cs: bool = False, block=(1, 1), median: int = 0):
         """Selects the variants of the stage (centre-symmetric census, SGBM

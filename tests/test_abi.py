@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -74,6 +75,20 @@ def test_null_handles_are_rejected(lib):
     assert lib.simsense_set_option(None, 1, 0) == -1
     assert lib.simsense_set_noise(None, 1, -0.231, 0.83, 3.98, 0.254, 1) == -1
     assert lib.simsense_destroy(None) == 0
+
+
+def test_geometry_calls_reject_bad_arguments(lib):
+    from paper_2201_11924_gb300 import simsense
+    import oracle
+    fake = ctypes.c_void_p(0x1000)
+    cam = simsense.camera_t(oracle.camera(300.0, 300.0, 10.0, 10.0))
+    bad = simsense.camera_t(oracle.camera(0.0, 300.0, 10.0, 10.0))
+    assert lib.simsense_set_rectify(None, ctypes.byref(cam), ctypes.byref(cam)) == -1
+    assert lib.simsense_rectify(None, fake, 8, 8, ctypes.byref(cam), None) == -1
+    assert lib.simsense_rectify(fake, fake, 0, 8, ctypes.byref(cam), None) == -1
+    assert lib.simsense_rectify(fake, fake, 8, 8, ctypes.byref(bad), None) == -1
+    reg = simsense.registration_t(100.0, 100.0, 4.0, 4.0, 100.0, 100.0, 4.0, 4.0, np.eye(3), [0, 0, 0], 0, 8)
+    assert lib.simsense_register_depth(fake, 8, 8, ctypes.byref(reg), fake, None) == -1
 
 
 @pytest.mark.parametrize("W,H,k,theta,sigma", [
