@@ -118,10 +118,13 @@ struct Magic {
     uint32_t m[82];
 };
 
-template <int N>
+// BW, BH: the block size, compile-time so the taps unroll (their shared-
+// memory reads are issued together instead of one dependent load at a time).
+template <int BW, int BH, int N>
 __global__ void __launch_bounds__(256)
-block_cost_kernel(PairTable<N> pt, int W, int H, int Dp, int bw, int bh, Magic mg)
+block_cost_kernel(PairTable<N> pt, int W, int H, int Dp, Magic mg)
 {
+    constexpr int bw = BW, bh = BH;
     extern __shared__ __align__(16) uint8_t seg[];     // bh x (kBlkPix + bw - 1) x Dp
     const uint8_t* __restrict__ raw = pt.p[blockIdx.z].vol;
     uint32_t* __restrict__ out = reinterpret_cast<uint32_t*>(pt.p[blockIdx.z].cost);
@@ -146,7 +149,9 @@ block_cost_kernel(PairTable<N> pt, int W, int H, int Dp, int bw, int bh, Magic m
         const int x = x0 + px;
         if (x >= W) break;                             // i grows with px
         uint32_t ev = 0, od = 0;                       // (b0, b2) and (b1, b3) sums
+#pragma unroll
         for (int r = 0; r < bh; r++)
+#pragma unroll
             for (int u = 0; u < bw; u++) {
                 const uint32_t v = s32[(r * span + px + u) * words + w];
                 ev += v & 0x00ff00ffu;
@@ -169,11 +174,19 @@ cudaError_t block_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStrea
     Magic mg{};
     for (uint32_t k = 1; k < 82; k++) mg.m[k] = (uint32_t)(0x100000000ull / k) + 1u;
     const size_t smem = (size_t)p.block_h * (kBlkPix + p.block_w - 1) * p.Dp;
-    auto kernel = block_cost_kernel<N>;
+    using K = void (*)(PairTable<N>, int, int, int, Magic);
+    // odd block sizes 1..7 in each direction
+    static constexpr K table[4][4] = {
+        {block_cost_kernel<1, 1, N>, block_cost_kernel<3, 1, N>, block_cost_kernel<5, 1, N>, block_cost_kernel<7, 1, N>},
+        {block_cost_kernel<1, 3, N>, block_cost_kernel<3, 3, N>, block_cost_kernel<5, 3, N>, block_cost_kernel<7, 3, N>},
+        {block_cost_kernel<1, 5, N>, block_cost_kernel<3, 5, N>, block_cost_kernel<5, 5, N>, block_cost_kernel<7, 5, N>},
+        {block_cost_kernel<1, 7, N>, block_cost_kernel<3, 7, N>, block_cost_kernel<5, 7, N>, block_cost_kernel<7, 7, N>},
+    };
+    const K kernel = table[p.block_h / 2][p.block_w / 2];
     cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.W + kBlkPix - 1) / kBlkPix, p.H, n);
-    kernel<<<grid, 256, smem, s>>>(pt, p.W, p.H, p.Dp, p.block_w, p.block_h, mg);
+    kernel<<<grid, 256, smem, s>>>(pt, p.W, p.H, p.Dp, mg);
     return cudaGetLastError();
 }
 
