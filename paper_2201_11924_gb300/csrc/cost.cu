@@ -120,18 +120,20 @@ struct Magic {
 
 // BW, BH: the block size, compile-time so the taps unroll (their shared-
 // memory reads are issued together instead of one dependent load at a time).
-template <int BW, int BH, int N>
+template <int BW, int BH, int DP, int N>
 __global__ void __launch_bounds__(256)
-block_cost_kernel(PairTable<N> pt, int W, int H, int Dp, Magic mg)
+block_cost_kernel(PairTable<N> pt, int W, int H, Magic mg)
 {
-    constexpr int bw = BW, bh = BH;
+    // the block size and the disparity pitch are compile-time, so the taps
+    // unroll and the index arithmetic divides by constants
+    constexpr int bw = BW, bh = BH, Dp = DP;
     extern __shared__ __align__(16) uint8_t seg[];     // bh x (kBlkPix + bw - 1) x Dp
     const uint8_t* __restrict__ raw = pt.p[blockIdx.z].vol;
     uint32_t* __restrict__ out = reinterpret_cast<uint32_t*>(pt.p[blockIdx.z].cost);
     const int y = blockIdx.y, x0 = blockIdx.x * kBlkPix;
     const int rx = bw >> 1, ry = bh >> 1;
-    const int span = kBlkPix + bw - 1;                 // pixels per staged row
-    const int vec = Dp >> 4;                           // 16-byte vectors per pixel
+    constexpr int span = kBlkPix + bw - 1;             // pixels per staged row
+    constexpr int vec = Dp >> 4;                       // 16-byte vectors per pixel
     for (int i = threadIdx.x; i < bh * span * vec; i += blockDim.x) {
         const int v = i % vec, px = (i / vec) % span, r = i / (vec * span);
         const int xx = x0 - rx + px, yy = y - ry + r;
@@ -141,7 +143,7 @@ block_cost_kernel(PairTable<N> pt, int W, int H, int Dp, Magic mg)
         reinterpret_cast<uint4*>(seg)[(r * span + px) * vec + v] = val;
     }
     __syncthreads();
-    const int words = Dp >> 2;
+    constexpr int words = Dp >> 2;
     const uint32_t* s32 = reinterpret_cast<const uint32_t*>(seg);
     const int ylo = max(y - ry, 0), yhi = min(y + ry, H - 1);
     for (int i = threadIdx.x; i < kBlkPix * words; i += blockDim.x) {
@@ -167,6 +169,34 @@ block_cost_kernel(PairTable<N> pt, int W, int H, int Dp, Magic mg)
 }
 
 template <int N>
+using K = void (*)(PairTable<N>, int, int, Magic);
+
+template <int BW, int BH, int N>
+K<N> block_kernel_dp(int Dp)
+{
+    switch (Dp) {
+        case 64: return block_cost_kernel<BW, BH, 64, N>;
+        case 128: return block_cost_kernel<BW, BH, 128, N>;
+        case 192: return block_cost_kernel<BW, BH, 192, N>;
+        default: return block_cost_kernel<BW, BH, 256, N>;
+    }
+}
+
+// odd block sizes 1..7 in each direction
+template <int N>
+K<N> block_kernel_for(const Params& p)
+{
+    using F = K<N> (*)(int);
+    static constexpr F table[4][4] = {
+        {block_kernel_dp<1, 1, N>, block_kernel_dp<3, 1, N>, block_kernel_dp<5, 1, N>, block_kernel_dp<7, 1, N>},
+        {block_kernel_dp<1, 3, N>, block_kernel_dp<3, 3, N>, block_kernel_dp<5, 3, N>, block_kernel_dp<7, 3, N>},
+        {block_kernel_dp<1, 5, N>, block_kernel_dp<3, 5, N>, block_kernel_dp<5, 5, N>, block_kernel_dp<7, 5, N>},
+        {block_kernel_dp<1, 7, N>, block_kernel_dp<3, 7, N>, block_kernel_dp<5, 7, N>, block_kernel_dp<7, 7, N>},
+    };
+    return table[p.block_h / 2][p.block_w / 2](p.Dp);
+}
+
+template <int N>
 cudaError_t block_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s)
 {
     PairTable<N> pt{};
@@ -174,19 +204,11 @@ cudaError_t block_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStrea
     Magic mg{};
     for (uint32_t k = 1; k < 82; k++) mg.m[k] = (uint32_t)(0x100000000ull / k) + 1u;
     const size_t smem = (size_t)p.block_h * (kBlkPix + p.block_w - 1) * p.Dp;
-    using K = void (*)(PairTable<N>, int, int, int, Magic);
-    // odd block sizes 1..7 in each direction
-    static constexpr K table[4][4] = {
-        {block_cost_kernel<1, 1, N>, block_cost_kernel<3, 1, N>, block_cost_kernel<5, 1, N>, block_cost_kernel<7, 1, N>},
-        {block_cost_kernel<1, 3, N>, block_cost_kernel<3, 3, N>, block_cost_kernel<5, 3, N>, block_cost_kernel<7, 3, N>},
-        {block_cost_kernel<1, 5, N>, block_cost_kernel<3, 5, N>, block_cost_kernel<5, 5, N>, block_cost_kernel<7, 5, N>},
-        {block_cost_kernel<1, 7, N>, block_cost_kernel<3, 7, N>, block_cost_kernel<5, 7, N>, block_cost_kernel<7, 7, N>},
-    };
-    const K kernel = table[p.block_h / 2][p.block_w / 2];
+    const K<N> kernel = block_kernel_for<N>(p);
     cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
     if (e != cudaSuccess) return e;
     dim3 grid((p.W + kBlkPix - 1) / kBlkPix, p.H, n);
-    kernel<<<grid, 256, smem, s>>>(pt, p.W, p.H, p.Dp, mg);
+    kernel<<<grid, 256, smem, s>>>(pt, p.W, p.H, mg);
     return cudaGetLastError();
 }
 
