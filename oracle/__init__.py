@@ -71,6 +71,8 @@ def _load():
             lib.oracle_philox4x64.argtypes = [P, P, P]
             lib.oracle_philox4x64.restype = None
             lib.oracle_noise.argtypes = [P, I, I, Dd, Dd, Dd, Dd, U64, U32, U32, P, P, P]
+            lib.oracle_render.argtypes = [P, I, P, P, P, P, P, P]
+            lib.oracle_render.restype = ctypes.c_int
             lib.oracle_rectify.argtypes = [P, I, I, P, P]
             lib.oracle_register.argtypes = [P, I, I, Dd, Dd, Dd, Dd, P, P, I, I]
             lib.oracle_rectify.restype = ctypes.c_int
@@ -230,6 +232,39 @@ def register(depth, fx, fy, cx, cy, fx2, fy2, cx2, cy2, R, t, W2, H2) -> np.ndar
     _check(_load().oracle_register(_ptr(depth), W, H, float(fx), float(fy), float(cx), float(cy), _ptr(reg),
                                    _ptr(out), W2, H2), "register")
     return out
+
+
+PRIM_DTYPE = np.dtype([("kind", np.int32), ("pad", np.int32), ("c", np.float64, 3), ("u", np.float64, 3),
+                       ("v", np.float64, 3), ("radius", np.float64), ("albedo", np.float64),
+                       ("metallic", np.float64), ("roughness", np.float64), ("transmission", np.float64)])
+RENDER_DTYPE = np.dtype([("W", np.int32), ("H", np.int32), ("f", np.float64), ("cx", np.float64),
+                         ("cy", np.float64), ("baseline", np.float64), ("proj", np.float64, 3), ("pf", np.float64),
+                         ("pcx", np.float64), ("pcy", np.float64), ("PW", np.int32), ("PH", np.int32),
+                         ("power", np.float64), ("ambient", np.float64), ("gain", np.float64)])
+
+
+def sphere(c, radius, albedo=0.8, metallic=0.0, roughness=0.5, transmission=0.0):
+    return (0, 0, c, (0, 0, 0), (0, 0, 0), radius, albedo, metallic, roughness, transmission)
+
+
+def rectangle(c, u, v, albedo=0.8, metallic=0.0, roughness=0.5, transmission=0.0):
+    return (1, 0, c, u, v, 0.0, albedo, metallic, roughness, transmission)
+
+
+def render(prims, pattern, W, H, f, cx, cy, baseline, proj, pf, pcx, pcy, power, ambient, gain):
+    """IR images (left, right uint8) and their values before rounding (float64)
+    of a scene of spheres and rectangles lit by a textured projector."""
+    pr = np.array(list(prims), dtype=PRIM_DTYPE)
+    pattern = np.ascontiguousarray(pattern, dtype=np.uint8)
+    PH, PW = pattern.shape
+    rp = np.array([(W, H, f, cx, cy, baseline, proj, pf, pcx, pcy, PW, PH, power, ambient, gain)], dtype=RENDER_DTYPE)
+    left = np.empty((H, W), dtype=np.uint8)
+    right = np.empty((H, W), dtype=np.uint8)
+    lf = np.empty((H, W), dtype=np.float64)
+    rf = np.empty((H, W), dtype=np.float64)
+    _check(_load().oracle_render(_ptr(pr), len(pr), _ptr(rp), _ptr(pattern), _ptr(left), _ptr(right), _ptr(lf),
+                                 _ptr(rf)), "render")
+    return left, right, lf, rf
 
 
 def compute(left, right, D, ww, wh, P1, P2, paths, uniq, lr_max_diff, subpixel, f, baseline,

@@ -74,6 +74,28 @@
  *    there (a z-buffer); fp64 with + - * / only, Z' rounded to fp32; RGB
  *    pixels no depth pixel reaches stay 0.
  *
+ * IR rendering of analytic scenes (Sec. VI-A/VI-B; the paper renders with
+ *  ray tracing in Vulkan, here a direct-light ray caster states the same
+ *  image formation).  Readings:
+ *  - a rectified pinhole pair (left camera at the origin, right at
+ *    (b, 0, 0), both looking along +z; f, cx, cy) casts one ray per pixel
+ *    centre; the nearest hit among spheres and rectangles wins (ties to the
+ *    lower index); no hit gives 0;
+ *  - the projector is a textured spot light at a point with its own
+ *    pinhole (pf, pcx, pcy) looking along +z; a lit point receives
+ *    E = power * pattern / 255 * (n.i) / dist^2, pattern sampled at the
+ *    nearest texel, 0 outside the texture or when a shadow ray to the
+ *    projector meets another surface;
+ *  - BSDF mix of Sec. VI-A: f = w_d f_d + (1 - w_d) f_s, w_d = (1 - metallic)
+ *    (1 - transmission), f_d = albedo / pi (Lambert), f_s = the GGX
+ *    microfacet term D F G / (4 (n.i)(n.o)) with alpha = roughness^2,
+ *    D = alpha^2 / (pi ((n.h)^2 (alpha^2 - 1) + 1)^2), Smith G1(x) =
+ *    2x / (x + sqrt(alpha^2 + (1 - alpha^2) x^2)), Schlick F with
+ *    F0 = 0.04 (1 - metallic) + albedo * metallic; no refracted light;
+ *  - radiance L = f E + ambient * albedo, pixel = gain * L rounded half to
+ *    even and clamped to [0, 255];
+ *  - all in fp64 with + - * / and sqrt only, in a fixed order.
+ *
  * Variants Sec. VI-D also names (optional in the stage):
  *  - centre-symmetric census (CSCT): for every offset o of the window that
  *    precedes the centre in raster order, bit = [I(p+o) < I(p-o)]; a pair
@@ -541,6 +563,152 @@ int oracle_register(const float* depth, int W, int H, double fx, double fy, doub
             float z = (float)Z2;
             if (out[k] == 0.0f || z < out[k]) out[k] = z;
         }
+    return ORACLE_OK;
+}
+
+/* ---------------------------------------------------------- IR rendering */
+
+typedef struct {
+    int kind;                       /* 0 sphere (c, radius), 1 rectangle (c, half-axes u, v) */
+    int pad;
+    double c[3], u[3], v[3], radius;
+    double albedo, metallic, roughness, transmission;
+} oracle_prim;
+
+typedef struct {
+    int W, H;
+    double f, cx, cy, baseline;     /* rectified camera pair */
+    double proj[3];                 /* projector centre */
+    double pf, pcx, pcy;            /* projector intrinsics */
+    int PW, PH;                     /* pattern size */
+    double power, ambient, gain;
+} oracle_render_params;
+
+static double dot3(const double* a, const double* b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* Ray o + t d against one primitive: the smallest t > eps, else -1. */
+static double hit_prim(const oracle_prim* q, const double* o, const double* d)
+{
+    const double eps = 1e-9;
+    if (q->kind == 0) {
+        double oc[3] = {o[0] - q->c[0], o[1] - q->c[1], o[2] - q->c[2]};
+        double a = dot3(d, d), b = 2.0 * dot3(d, oc), cc = dot3(oc, oc) - q->radius * q->radius;
+        double disc = b * b - 4.0 * a * cc;
+        if (disc < 0.0) return -1.0;
+        double sq = sqrt(disc);
+        double t = (-b - sq) / (2.0 * a);
+        if (t > eps) return t;
+        t = (-b + sq) / (2.0 * a);
+        return t > eps ? t : -1.0;
+    }
+    double n[3] = {q->u[1] * q->v[2] - q->u[2] * q->v[1], q->u[2] * q->v[0] - q->u[0] * q->v[2],
+                   q->u[0] * q->v[1] - q->u[1] * q->v[0]};
+    double den = dot3(d, n);
+    if (den == 0.0) return -1.0;
+    double co[3] = {q->c[0] - o[0], q->c[1] - o[1], q->c[2] - o[2]};
+    double t = dot3(co, n) / den;
+    if (!(t > eps)) return -1.0;
+    double p[3] = {o[0] + t * d[0] - q->c[0], o[1] + t * d[1] - q->c[1], o[2] + t * d[2] - q->c[2]};
+    double s = dot3(p, q->u) / dot3(q->u, q->u), w = dot3(p, q->v) / dot3(q->v, q->v);
+    if (s < -1.0 || s > 1.0 || w < -1.0 || w > 1.0) return -1.0;
+    return t;
+}
+
+static double shade(const oracle_prim* prims, int n, const oracle_render_params* rp, const uint8_t* pattern,
+                    const double* o, const double* d)
+{
+    const double PI = 3.14159265358979323846;
+    int best = -1;
+    double tb = 0.0;
+    for (int k = 0; k < n; k++) {
+        double t = hit_prim(&prims[k], o, d);
+        if (t > 0.0 && (best < 0 || t < tb)) { best = k; tb = t; }
+    }
+    if (best < 0) return 0.0;
+    const oracle_prim* q = &prims[best];
+    double p[3] = {o[0] + tb * d[0], o[1] + tb * d[1], o[2] + tb * d[2]};
+    double nn[3];
+    if (q->kind == 0) {
+        nn[0] = (p[0] - q->c[0]) / q->radius; nn[1] = (p[1] - q->c[1]) / q->radius; nn[2] = (p[2] - q->c[2]) / q->radius;
+    } else {
+        double m[3] = {q->u[1] * q->v[2] - q->u[2] * q->v[1], q->u[2] * q->v[0] - q->u[0] * q->v[2],
+                       q->u[0] * q->v[1] - q->u[1] * q->v[0]};
+        double len = sqrt(dot3(m, m));
+        nn[0] = m[0] / len; nn[1] = m[1] / len; nn[2] = m[2] / len;
+        if (dot3(nn, d) > 0.0) { nn[0] = -nn[0]; nn[1] = -nn[1]; nn[2] = -nn[2]; }
+    }
+    double L = rp->ambient * q->albedo;
+    /* projector light */
+    double li[3] = {rp->proj[0] - p[0], rp->proj[1] - p[1], rp->proj[2] - p[2]};
+    double dist2 = dot3(li, li), dist = sqrt(dist2);
+    double iv[3] = {li[0] / dist, li[1] / dist, li[2] / dist};
+    double ni = dot3(nn, iv);
+    double X[3] = {p[0] - rp->proj[0], p[1] - rp->proj[1], p[2] - rp->proj[2]};
+    if (ni > 0.0 && X[2] > 0.0) {
+        int lit = 1;
+        for (int k = 0; k < n && lit; k++) {
+            if (k == best) continue;
+            double t = hit_prim(&prims[k], p, li);
+            if (t > 0.0 && t < 1.0) lit = 0;
+        }
+        double up = rp->pf * (X[0] / X[2]) + rp->pcx, vp = rp->pf * (X[1] / X[2]) + rp->pcy;
+        double fu = floor(up + 0.5), fv = floor(vp + 0.5);
+        double pat = 0.0;
+        if (fu >= 0.0 && fu < (double)rp->PW && fv >= 0.0 && fv < (double)rp->PH)
+            pat = (double)pattern[(int)fv * rp->PW + (int)fu] / 255.0;
+        if (lit && pat > 0.0) {
+            double E = rp->power * pat * ni / dist2;
+            double ov[3] = {o[0] - p[0], o[1] - p[1], o[2] - p[2]};
+            double ol = sqrt(dot3(ov, ov));
+            ov[0] = ov[0] / ol; ov[1] = ov[1] / ol; ov[2] = ov[2] / ol;
+            double no = dot3(nn, ov);
+            double wd = (1.0 - q->metallic) * (1.0 - q->transmission);
+            double fd = q->albedo / PI;
+            double fs = 0.0;
+            if (no > 0.0) {
+                double hv[3] = {iv[0] + ov[0], iv[1] + ov[1], iv[2] + ov[2]};
+                double hl = sqrt(dot3(hv, hv));
+                hv[0] = hv[0] / hl; hv[1] = hv[1] / hl; hv[2] = hv[2] / hl;
+                double a = q->roughness * q->roughness, a2 = a * a;
+                double nh = dot3(nn, hv);
+                double den = nh * nh * (a2 - 1.0) + 1.0;
+                double D = a2 / (PI * den * den);
+                double g1i = 2.0 * ni / (ni + sqrt(a2 + (1.0 - a2) * ni * ni));
+                double g1o = 2.0 * no / (no + sqrt(a2 + (1.0 - a2) * no * no));
+                double F0 = 0.04 * (1.0 - q->metallic) + q->albedo * q->metallic;
+                double vh = dot3(ov, hv);
+                double m1 = 1.0 - vh, m2 = m1 * m1;
+                double F = F0 + (1.0 - F0) * (m2 * m2 * m1);
+                fs = D * F * (g1i * g1o) / (4.0 * ni * no);
+            }
+            L = L + (wd * fd + (1.0 - wd) * fs) * E;
+        }
+    }
+    return rp->gain * L;
+}
+
+/* IR images of both cameras.  prims: n primitives; pattern: PH x PW bytes;
+ * left, right: H x W bytes; left_f, right_f (may be NULL): gain * L before
+ * rounding. */
+int oracle_render(const oracle_prim* prims, int n, const oracle_render_params* rp, const uint8_t* pattern,
+                  uint8_t* left, uint8_t* right, double* left_f, double* right_f)
+{
+    if (!prims || n < 0 || !rp || !pattern || !left || !right || rp->W <= 0 || rp->H <= 0) return ORACLE_BAD_ARG;
+    for (int view = 0; view < 2; view++) {
+        double o[3] = {view ? rp->baseline : 0.0, 0.0, 0.0};
+        uint8_t* img = view ? right : left;
+        double* imf = view ? right_f : left_f;
+        for (int v = 0; v < rp->H; v++)
+            for (int u = 0; u < rp->W; u++) {
+                double d[3] = {((double)u - rp->cx) / rp->f, ((double)v - rp->cy) / rp->f, 1.0};
+                double val = shade(prims, n, rp, pattern, o, d);
+                double qv = nearbyint(val);
+                if (qv < 0.0) qv = 0.0;
+                if (qv > 255.0) qv = 255.0;
+                img[v * rp->W + u] = (uint8_t)qv;
+                if (imf) imf[v * rp->W + u] = val;
+            }
+    }
     return ORACLE_OK;
 }
 

@@ -1,0 +1,105 @@
+"""Pins of the oracle's IR renderer (arxiv 2201.11924 Sec. VI-A/VI-B: a
+textured spot-light projector and the BSDF mix f = w_d f_d + (1 - w_d) f_s,
+w_d = (1 - metallic)(1 - transmission); the direct-light ray caster and its
+parameters are readings).
+
+Pins: the cosine-cubed falloff of a fronto-parallel Lambertian wall lit from
+the camera centre (closed form), the stereo shift d = f b / Z between the two
+views, projector shadows against an independent ray-sphere test, linearity of
+the mix in the transmission weight, and the specular highlight of a glossy
+metal sphere at the point facing the light."""
+import numpy as np
+import pytest
+
+import oracle
+
+W, H, F = 80, 60, 60.0
+CX, CY = 40.0, 30.0
+
+
+def _wall(Z, **mat):
+    return oracle.rectangle((0, 0, Z), (5, 0, 0), (0, 5, 0), **mat)
+
+
+def _render(prims, pattern, baseline=0.05, proj=(0, 0, 0), power=1.0, ambient=0.05, gain=400.0):
+    return oracle.render(prims, pattern, W, H, F, CX, CY, baseline, proj, F, CX, CY, power, ambient, gain)
+
+
+def test_lambert_wall_follows_the_cosine_cubed_law():
+    rng = np.random.default_rng(1)
+    pat = rng.integers(1, 256, (H, W), dtype=np.uint8)
+    Z, albedo, power, amb, gain = 1.3, 0.7, 2.0, 0.05, 400.0
+    _, _, lf, _ = _render([_wall(Z, albedo=albedo)], pat, power=power, ambient=amb, gain=gain)
+    us, vs = np.meshgrid(np.arange(W), np.arange(H))
+    dn = np.sqrt(((us - CX) / F) ** 2 + ((vs - CY) / F) ** 2 + 1.0)      # |d| of the pixel ray
+    want = gain * (albedo / np.pi * power * (pat / 255.0) / (Z * Z * dn ** 3) + amb * albedo)
+    np.testing.assert_allclose(lf, want, rtol=1e-12)
+
+
+@pytest.mark.parametrize("Z", [0.5, 1.0])
+def test_right_view_is_the_left_view_shifted_by_the_disparity(Z):
+    # Lambertian radiance does not depend on the viewer: right(u) = left(u + f b / Z)
+    rng = np.random.default_rng(2)
+    pat = rng.integers(1, 256, (H, W), dtype=np.uint8)
+    b = 5.0 * Z / F                                  # an integer disparity of 5 px
+    _, _, lf, rf = _render([_wall(Z)], pat, baseline=b)
+    np.testing.assert_allclose(rf[:, :W - 5], lf[:, 5:], rtol=1e-9)
+
+
+def test_projector_shadow_of_a_sphere():
+    pat = np.full((H, W), 255, dtype=np.uint8)
+    Z, c, r = 1.0, np.array([0.05, 0.02, 0.5]), 0.08
+    proj = np.array([0.02, 0.0, 0.0])
+    amb, albedo, gain = 0.05, 0.6, 400.0
+    wall = _wall(Z, albedo=albedo)
+    ball = oracle.sphere(tuple(c), r, albedo=0.3)
+    _, _, lf, _ = _render([wall, ball], pat, proj=tuple(proj), ambient=amb, gain=gain)
+    us, vs = np.meshgrid(np.arange(W), np.arange(H))
+    for u, v in [(int(x), int(y)) for x, y in zip(us.ravel()[::37], vs.ravel()[::37])]:
+        d = np.array([(u - CX) / F, (v - CY) / F, 1.0])
+        # the camera ray first: pixels that see the sphere are not wall pixels
+        oc = -c
+        bq, cq = 2 * d @ oc, oc @ oc - r * r
+        if bq * bq - 4 * (d @ d) * cq >= 0:
+            continue
+        p = Z * d                                    # the wall point
+        X = p - proj                                 # outside the projector's texture: unlit anyway
+        up, vp = np.floor(F * X[0] / X[2] + CX + 0.5), np.floor(F * X[1] / X[2] + CY + 0.5)
+        if not (0 <= up < W and 0 <= vp < H):
+            continue
+        L = proj - p                                 # towards the projector: does it pass the sphere?
+        pc = p - c
+        a2, b2, c2 = L @ L, 2 * L @ pc, pc @ pc - r * r
+        disc = b2 * b2 - 4 * a2 * c2
+        shadowed = disc >= 0 and 0 < (-b2 - np.sqrt(disc)) / (2 * a2) < 1
+        if shadowed:
+            assert abs(lf[v, u] - gain * amb * albedo) < 1e-9, (u, v)
+        else:
+            assert lf[v, u] > gain * amb * albedo + 1.0, (u, v)
+
+
+def test_mix_is_linear_in_the_transmission_weight():
+    rng = np.random.default_rng(3)
+    pat = rng.integers(1, 256, (H, W), dtype=np.uint8)
+    ball = dict(c=(0.0, 0.0, 0.8), radius=0.3, albedo=0.6, metallic=0.0, roughness=0.4)
+    out = {}
+    for t in (0.0, 0.35, 1.0):
+        _, _, lf, _ = _render([_wall(1.5), oracle.sphere(transmission=t, **ball)], pat, ambient=0.0)
+        out[t] = lf
+    np.testing.assert_allclose(out[0.35], 0.65 * out[0.0] + 0.35 * out[1.0], rtol=1e-9, atol=1e-9)
+
+
+def test_glossy_metal_highlight_faces_the_light():
+    pat = np.full((H, W), 255, dtype=np.uint8)
+    c = (0.03, -0.02, 0.7)
+    _, _, lf, _ = _render([oracle.sphere(c, 0.2, albedo=0.9, metallic=1.0, roughness=0.15)], pat, ambient=0.0)
+    v, u = np.unravel_index(np.argmax(lf), lf.shape)
+    # projector at the camera centre: the mirror point lies on the line to the centre
+    assert abs(u - (F * c[0] / c[2] + CX)) <= 1 and abs(v - (F * c[1] / c[2] + CY)) <= 1
+
+
+def test_rays_that_miss_give_zero_and_rounding():
+    pat = np.full((H, W), 255, dtype=np.uint8)
+    l, r, lf, rf = _render([oracle.sphere((0, 0, 1.0), 0.1)], pat)
+    assert l[0, 0] == 0 and lf[0, 0] == 0.0
+    assert np.array_equal(l, np.clip(np.rint(lf), 0, 255).astype(np.uint8))
