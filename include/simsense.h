@@ -295,6 +295,53 @@ int simsense_rectify(const uint8_t* raw, uint8_t* out, int W, int H, const simse
 int simsense_register_depth(const float* depth, int W, int H, const simsense_registration_t* reg, float* out,
                             struct CUstream_st* stream);
 
+/*
+ * IR image formation of analytic scenes (arxiv 2201.11924 Sec. VI-A/VI-B: the
+ * projector is "a textured spot light", surfaces use the BSDF mix
+ * f = w_d f_d + (1 - w_d) f_s with w_d = (1 - metallic)(1 - transmission),
+ * f_d Lambertian, f_s GGX, plus a weak ambient light).  The paper renders with
+ * a Vulkan path tracer; the library's reading is a direct-light ray caster:
+ *  - cameras: a rectified pinhole pair (f, cx, cy in pixels), the left at the
+ *    origin and the right at (baseline, 0, 0), both looking along +z; one ray
+ *    per pixel centre, the nearest hit among the primitives (ties to the lower
+ *    index), 0 where nothing is hit;
+ *  - primitives: kind 0 sphere (centre c, radius), kind 1 rectangle (centre
+ *    c, half-axes u and v, assumed orthogonal); albedo, metallic, roughness,
+ *    transmission in [0, 1];
+ *  - projector at proj looking along +z, pinhole (pf, pcx, pcy), texture
+ *    pattern PH x PW bytes sampled at the nearest texel; a point receives
+ *    E = power * pattern / 255 * (n.i) / dist^2 unless the texel lies outside
+ *    the texture or another primitive is between it and the projector;
+ *  - f_s = D F G / (4 (n.i)(n.o)), alpha = roughness^2, D GGX, Smith G1,
+ *    Schlick F with F0 = 0.04 (1 - metallic) + albedo metallic; no refracted
+ *    or indirect light;
+ *  - pixel = gain * (f E + ambient * albedo), rounded half to even, clamped
+ *    to [0, 255]; fp64 with correctly rounded + - * / and sqrt in a fixed
+ *    order.
+ * prims: n (0..4096) device primitives; pattern, left, right: device bytes;
+ * rp: host pointer.  Asynchronous on stream; SIMSENSE_ERR_INVALID_ARG for
+ * NULL pointers, sizes outside 1..16384, non-finite parameters or a zero
+ * focal length.
+ */
+typedef struct {
+    int kind;                       /* 0 sphere, 1 rectangle */
+    int pad;
+    double c[3], u[3], v[3], radius;
+    double albedo, metallic, roughness, transmission;
+} simsense_primitive_t;
+
+typedef struct {
+    int W, H;
+    double f, cx, cy, baseline;
+    double proj[3];
+    double pf, pcx, pcy;
+    int PW, PH;
+    double power, ambient, gain;
+} simsense_render_t;
+
+int simsense_render_ir(const simsense_primitive_t* prims, int n, const simsense_render_t* rp,
+                       const uint8_t* pattern, uint8_t* left, uint8_t* right, struct CUstream_st* stream);
+
 /* Set an option (SIMSENSE_OPT_*).  Takes effect at the next compute call. */
 int simsense_set_option(simsense_t h, int opt, int value);
 

@@ -59,6 +59,48 @@ class RegistrationT(ctypes.Structure):
                [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3), ("W2", ctypes.c_int), ("H2", ctypes.c_int)]
 
 
+class RenderT(ctypes.Structure):
+    """simsense_render_t: camera pair, projector and image formation constants."""
+    _fields_ = [("W", ctypes.c_int), ("H", ctypes.c_int)] + \
+               [(n, ctypes.c_double) for n in ("f", "cx", "cy", "baseline")] + [("proj", ctypes.c_double * 3)] + \
+               [(n, ctypes.c_double) for n in ("pf", "pcx", "pcy")] + [("PW", ctypes.c_int), ("PH", ctypes.c_int)] + \
+               [(n, ctypes.c_double) for n in ("power", "ambient", "gain")]
+
+
+# simsense_primitive_t as a numpy record: kind (0 sphere, 1 rectangle), centre
+# c, half-axes u, v, radius, then the material
+PRIMITIVE_DTYPE = [("kind", "<i4"), ("pad", "<i4"), ("c", "<f8", 3), ("u", "<f8", 3), ("v", "<f8", 3),
+                   ("radius", "<f8"), ("albedo", "<f8"), ("metallic", "<f8"), ("roughness", "<f8"),
+                   ("transmission", "<f8")]
+
+
+def render_ir(prims, pattern, W, H, f, cx, cy, baseline, proj, pf, pcx, pcy, power, ambient, gain, stream=None):
+    """IR images (left, right: H x W uint8 CUDA tensors) of a scene of spheres
+    and rectangles lit by a textured projector (Sec. VI-A/VI-B).  prims: a
+    sequence of primitive records (PRIMITIVE_DTYPE); pattern: PH x PW uint8
+    CUDA tensor."""
+    import numpy as np
+    import torch
+    rec = np.array([tuple(p) for p in prims], dtype=PRIMITIVE_DTYPE)
+    dev = pattern.device
+    pt = torch.from_numpy(rec.view(np.uint8).copy()).to(dev) if len(rec) else None
+    PH, PW = pattern.shape
+    _dev_ptr(pattern, torch.uint8, (PH, PW), "pattern")
+    rp = RenderT(int(W), int(H), float(f), float(cx), float(cy), float(baseline), (ctypes.c_double * 3)(*proj),
+                 float(pf), float(pcx), float(pcy), int(PW), int(PH), float(power), float(ambient), float(gain))
+    left = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    right = torch.empty((H, W), dtype=torch.uint8, device=dev)
+    rc = load().simsense_render_ir(ctypes.c_void_p(pt.data_ptr()) if pt is not None else None, len(rec),
+                                   ctypes.byref(rp), ctypes.c_void_p(pattern.data_ptr()),
+                                   ctypes.c_void_p(left.data_ptr()), ctypes.c_void_p(right.data_ptr()),
+                                   _stream_ptr(stream))
+    if rc != 0:
+        raise SimsenseError(rc, "simsense_render_ir")
+    if pt is not None and stream is not None:
+        pt.record_stream(stream)       # the primitive table outlives this call on that stream
+    return left, right
+
+
 def camera_t(values) -> CameraT:
     """A camera from the 22 numbers fx fy cx cy k1 k2 p1 p2 k3 R[9] rfx rfy rcx rcy."""
     v = [float(x) for x in values]
@@ -101,6 +143,8 @@ def load():
             lib.simsense_stage_name.argtypes = [I]
             lib.simsense_stage_name.restype = ctypes.c_char_p
             U64, U32 = ctypes.c_ulonglong, ctypes.c_uint
+            lib.simsense_render_ir.argtypes = [P, I, ctypes.POINTER(RenderT), P, P, P, P]
+            lib.simsense_render_ir.restype = ctypes.c_int
             lib.simsense_set_rectify.argtypes = [P, ctypes.POINTER(CameraT), ctypes.POINTER(CameraT)]
             lib.simsense_rectify.argtypes = [P, P, I, I, ctypes.POINTER(CameraT), P]
             lib.simsense_register_depth.argtypes = [P, I, I, ctypes.POINTER(RegistrationT), P, P]

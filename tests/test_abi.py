@@ -91,6 +91,19 @@ def test_geometry_calls_reject_bad_arguments(lib):
     assert lib.simsense_register_depth(fake, 8, 8, ctypes.byref(reg), fake, None) == -1
 
 
+def test_render_rejects_bad_arguments(lib):
+    from paper_2201_11924_gb300 import simsense
+    fake = ctypes.c_void_p(0x1000)
+    good = simsense.RenderT(8, 8, 10.0, 4.0, 4.0, 0.05, (ctypes.c_double * 3)(0, 0, 0), 10.0, 4.0, 4.0, 8, 8,
+                            1.0, 0.1, 100.0)
+    bad = simsense.RenderT(8, 8, 0.0, 4.0, 4.0, 0.05, (ctypes.c_double * 3)(0, 0, 0), 10.0, 4.0, 4.0, 8, 8,
+                           1.0, 0.1, 100.0)
+    assert lib.simsense_render_ir(fake, 1, ctypes.byref(bad), fake, fake, fake, None) == -1
+    assert lib.simsense_render_ir(None, 1, ctypes.byref(good), fake, fake, fake, None) == -1
+    assert lib.simsense_render_ir(fake, -1, ctypes.byref(good), fake, fake, fake, None) == -1
+    assert lib.simsense_render_ir(fake, 1, None, fake, fake, fake, None) == -1
+
+
 @pytest.mark.parametrize("W,H,k,theta,sigma", [
     (0, 8, 3.98, 0.254, 0.83),           # empty image
     (8, 8, 0.5, 0.254, 0.83),            # k < 1 (the rejection sampler needs k >= 1)
