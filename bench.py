@@ -326,6 +326,79 @@ def run_table2(args):
     return 0
 
 
+def _sim_scene(seed, W, H):
+    """A random analytic scene for the simulated sensor: a back wall, tilted
+    rectangles and spheres with random materials (Sec. VI-A)."""
+    rng = np.random.default_rng(seed)
+
+    def rect(c, u, v, **m):
+        return (1, 0, c, u, v, 0.0, m["albedo"], m["metallic"], m["roughness"], m["transmission"])
+
+    def sph(c, r, **m):
+        return (0, 0, c, (0, 0, 0), (0, 0, 0), r, m["albedo"], m["metallic"], m["roughness"], m["transmission"])
+
+    def mat():
+        return dict(albedo=rng.uniform(0.2, 1.0), metallic=rng.uniform(0, 0.6), roughness=rng.uniform(0.2, 0.9),
+                    transmission=rng.uniform(0, 0.3))
+    prims = [rect((0.0, 0.0, 2.0), (2.5, 0.0, 0.0), (0.0, 1.5, 0.0), albedo=0.7, metallic=0.0, roughness=0.8,
+                  transmission=0.0)]
+    for _ in range(6):
+        a, b = rng.uniform(-0.5, 0.5, 2)
+        prims.append(rect((rng.uniform(-0.7, 0.7), rng.uniform(-0.4, 0.4), rng.uniform(0.5, 1.8)),
+                          (rng.uniform(0.1, 0.4) * np.cos(a), 0.0, rng.uniform(0.1, 0.4) * np.sin(a)),
+                          (0.0, rng.uniform(0.1, 0.3) * np.cos(b), rng.uniform(0.1, 0.3) * np.sin(b)), **mat()))
+    for _ in range(8):
+        prims.append(sph((rng.uniform(-0.7, 0.7), rng.uniform(-0.4, 0.4), rng.uniform(0.4, 1.8)),
+                         rng.uniform(0.03, 0.15), **mat()))
+    return prims
+
+
+def run_sim(args):
+    """The whole simulated active-stereo sensor on the device: IR rendering of
+    an analytic scene with the projector pattern (Sec. VI-A/B), sensor noise
+    (Sec. VI-C) and the depth stage (Sec. VI-D); 1280 x 720, D = 128."""
+    import torch
+    from paper_2201_11924_gb300 import simsense
+    wl = dataclasses.replace(configs.HD_720, noise=True)
+    W, H = wl.W, wl.H
+    f = wl.f
+    dev = torch.device("cuda", 0)
+    pat = torch.from_numpy(((np.random.default_rng(11).random((H, W)) < 0.15) * 230 + 20).astype(np.uint8)).to(dev)
+    prims = _sim_scene(12, W, H)
+    ra = dict(W=W, H=H, f=f, cx=(W - 1) / 2, cy=(H - 1) / 2, baseline=wl.baseline, proj=(0.02, 0.0, 0.0), pf=f,
+              pcx=(W - 1) / 2, pcy=(H - 1) / 2, power=1.2, ambient=0.04, gain=350.0)
+    depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+    with simsense.SimSense.from_workload(wl) as m:
+        for _ in range(args.warmup):
+            l, r = simsense.render_ir(prims, pat, **ra)
+            m.compute(l, r, depth)
+        torch.cuda.synchronize()
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        for _ in range(args.steps):
+            l, r = simsense.render_ir(prims, pat, **ra)
+        e1.record()
+        for _ in range(args.steps):
+            m.compute(l, r, depth)
+        e2.record()
+        torch.cuda.synchronize()
+    render_ms = e0.elapsed_time(e1) / args.steps
+    depth_ms = e1.elapsed_time(e2) / args.steps
+    value = 1e3 / (render_ms + depth_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": render_ms + depth_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": "sim_1280x720_render15prims_noiseD415_D128_census7x7_8path",
+                   "l2": "no flush: each step renders and matches a full frame"},
+        "render_ms": render_ms, "depth_with_noise_ms": depth_ms,
+        # render, noise, census, cost, paths, select per frame
+        "gpu_launches": 6 * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batchmix(args):
     """The 64-pair batch of uneven sizes ({640x360 D64, 848x480 D96,
     1280x720 D128, 1280x720 D256}, 7x7 census, 8 paths): frames/s of one
@@ -457,9 +530,10 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-strip-rows", type=int, default=90)
-    ap.add_argument("--mode", default="plain", choices=["plain", "batchmix", "serve", "table2"],
+    ap.add_argument("--mode", default="plain", choices=["plain", "batchmix", "serve", "table2", "sim"],
                     help="plain: the default contract line; batchmix: the 64-pair mixed batch; "
                          "table2: the paper's Table 2 workload (960x540, rectified, registered to 1920x1080); "
+                         "sim: the whole simulated sensor on the device (render, noise, depth); "
                          "serve: the continuous-batching request loop")
     ap.add_argument("--serve-rate", type=float, default=4000.0, help="Poisson arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=8.0, help="trace length")
@@ -492,6 +566,8 @@ def main():
         return run_batchmix(args)
     if args.mode == "table2":
         return run_table2(args)
+    if args.mode == "sim":
+        return run_sim(args)
     if args.mode == "serve":
         return run_serve(args)
 
