@@ -103,64 +103,66 @@ cudaError_t cost_code(const Params& p, const PairPtrs* pairs, int n, cudaStream_
 // between the local regions of the two pixels): the per-pixel cost volume
 // `raw` averaged over the bw x bh block around each pixel (same d), over the
 // block's pixels inside the image, rounded half up, into `out`.
-// A block takes 32 pixels of one output row: it copies the bh input row
-// segments it needs (32 + bw - 1 pixels each, all Dp bytes, 16-byte vector
-// loads; pixels outside the image as 0) into shared memory, then a thread
-// takes one 4-byte word (4 disparities) of a pixel: lanes take consecutive
-// words of one pixel, so the shared-memory reads are conflict-free.  The
-// block sum of each byte is accumulated as two 16-bit pairs (at most
-// 49 x 255 < 2^16) and divided by the in-image pixel count n with a
-// multiply-high by floor(2^32 / n) + 1, exact for every numerator below 2^16
-// and n <= 81.
+// A block takes 32 pixels of one output row in two separable passes:
+//   1. for every staged column (32 + bw - 1 pixels) and 4-byte word of the
+//      disparity range, the sum over the bh input rows, kept in shared memory
+//      as two 16-bit pairs (bytes 0 and 2, bytes 1 and 3; at most 49 x 255 <
+//      2^16), so every input word is split into pairs once;
+//   2. for every output pixel and word, the sum of the bw staged columns and
+//      the division by the in-image pixel count n, a multiply-high by
+//      floor(2^32 / n) + 1, exact for every numerator below 2^16 and n <= 81.
+// Lanes take consecutive words of one pixel: coalesced loads, conflict-free
+// shared-memory accesses.
 constexpr int kBlkPix = 32;
 
 struct Magic {
     uint32_t m[82];
 };
 
-// BW, BH: the block size, compile-time so the taps unroll (their shared-
-// memory reads are issued together instead of one dependent load at a time).
+// BW, BH (the block) and DP (the disparity pitch) are compile-time, so the
+// taps unroll and the index arithmetic divides by constants.
 template <int BW, int BH, int DP, int N>
 __global__ void __launch_bounds__(256)
 block_cost_kernel(PairTable<N> pt, int W, int H, Magic mg)
 {
-    // the block size and the disparity pitch are compile-time, so the taps
-    // unroll and the index arithmetic divides by constants
-    constexpr int bw = BW, bh = BH, Dp = DP;
-    extern __shared__ __align__(16) uint8_t seg[];     // bh x (kBlkPix + bw - 1) x Dp
-    const uint8_t* __restrict__ raw = pt.p[blockIdx.z].vol;
+    constexpr int rx = BW / 2, ry = BH / 2;
+    constexpr int span = kBlkPix + BW - 1;             // staged columns
+    constexpr int words = DP / 4;                      // 4-byte words per pixel
+    __shared__ uint2 col[span * words];                // column sums (even pairs, odd pairs)
+    const uint32_t* __restrict__ raw = reinterpret_cast<const uint32_t*>(pt.p[blockIdx.z].vol);
     uint32_t* __restrict__ out = reinterpret_cast<uint32_t*>(pt.p[blockIdx.z].cost);
     const int y = blockIdx.y, x0 = blockIdx.x * kBlkPix;
-    const int rx = bw >> 1, ry = bh >> 1;
-    constexpr int span = kBlkPix + bw - 1;             // pixels per staged row
-    constexpr int vec = Dp >> 4;                       // 16-byte vectors per pixel
-    for (int i = threadIdx.x; i < bh * span * vec; i += blockDim.x) {
-        const int v = i % vec, px = (i / vec) % span, r = i / (vec * span);
-        const int xx = x0 - rx + px, yy = y - ry + r;
-        uint4 val = make_uint4(0, 0, 0, 0);
-        if (xx >= 0 && xx < W && yy >= 0 && yy < H)
-            val = __ldg(reinterpret_cast<const uint4*>(raw + ((size_t)yy * W + xx) * Dp) + v);
-        reinterpret_cast<uint4*>(seg)[(r * span + px) * vec + v] = val;
+    for (int i = threadIdx.x; i < span * words; i += blockDim.x) {
+        const int w = i % words, px = i / words;
+        const int xx = x0 - rx + px;
+        uint32_t ev = 0, od = 0;
+        if (xx >= 0 && xx < W) {
+#pragma unroll
+            for (int r = 0; r < BH; r++) {
+                const int yy = y - ry + r;
+                if (yy >= 0 && yy < H) {
+                    const uint32_t v = __ldg(raw + ((size_t)yy * W + xx) * words + w);
+                    ev += v & 0x00ff00ffu;
+                    od += (v >> 8) & 0x00ff00ffu;
+                }
+            }
+        }
+        col[i] = make_uint2(ev, od);
     }
     __syncthreads();
-    constexpr int words = Dp >> 2;
-    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(seg);
-    const int ylo = max(y - ry, 0), yhi = min(y + ry, H - 1);
+    const int rows = min(y + ry, H - 1) - max(y - ry, 0) + 1;
     for (int i = threadIdx.x; i < kBlkPix * words; i += blockDim.x) {
         const int w = i % words, px = i / words;
         const int x = x0 + px;
         if (x >= W) break;                             // i grows with px
-        uint32_t ev = 0, od = 0;                       // (b0, b2) and (b1, b3) sums
+        uint32_t ev = 0, od = 0;
 #pragma unroll
-        for (int r = 0; r < bh; r++)
-#pragma unroll
-            for (int u = 0; u < bw; u++) {
-                const uint32_t v = s32[(r * span + px + u) * words + w];
-                ev += v & 0x00ff00ffu;
-                od += (v >> 8) & 0x00ff00ffu;
-            }
-        const int xlo = max(x - rx, 0), xhi = min(x + rx, W - 1);
-        const uint32_t n = (uint32_t)((xhi - xlo + 1) * (yhi - ylo + 1));
+        for (int u = 0; u < BW; u++) {
+            const uint2 c = col[(px + u) * words + w];
+            ev += c.x;
+            od += c.y;
+        }
+        const uint32_t n = (uint32_t)((min(x + rx, W - 1) - max(x - rx, 0) + 1) * rows);
         const uint32_t m = mg.m[n], h = n >> 1;
         const uint32_t c0 = __umulhi((ev & 0xffffu) + h, m), c2 = __umulhi((ev >> 16) + h, m);
         const uint32_t c1 = __umulhi((od & 0xffffu) + h, m), c3 = __umulhi((od >> 16) + h, m);
@@ -203,12 +205,9 @@ cudaError_t block_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStrea
     for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
     Magic mg{};
     for (uint32_t k = 1; k < 82; k++) mg.m[k] = (uint32_t)(0x100000000ull / k) + 1u;
-    const size_t smem = (size_t)p.block_h * (kBlkPix + p.block_w - 1) * p.Dp;
     const K<N> kernel = block_kernel_for<N>(p);
-    cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
-    if (e != cudaSuccess) return e;
     dim3 grid((p.W + kBlkPix - 1) / kBlkPix, p.H, n);
-    kernel<<<grid, 256, smem, s>>>(pt, p.W, p.H, mg);
+    kernel<<<grid, 256, 0, s>>>(pt, p.W, p.H, mg);
     return cudaGetLastError();
 }
 
