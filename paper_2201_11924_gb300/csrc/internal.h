@@ -113,7 +113,7 @@ struct SelectDebug {
 // (n > kMaxBatch is split into several launches).
 cudaError_t launch_census(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s);
 cudaError_t launch_widen_codes(const Params& p, const void* codes, uint64_t* out, cudaStream_t s);
-cudaError_t launch_cost(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s);
+cudaError_t launch_cost(const Params& p, const PairPtrs* pairs, int n, int* status, cudaStream_t s);
 // SGBM block cost: pairs[i].vol holds the per-pixel cost volume on entry,
 // pairs[i].cost receives its block mean.
 cudaError_t launch_block_cost(const Params& p, const PairPtrs* pairs, int n, cudaStream_t s);

@@ -95,10 +95,10 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
         // path stage), their block mean to the cost volume
         PairPtrs raw = pair;
         raw.cost = s.paths;
-        if (e == cudaSuccess) e = launch_cost(p, &raw, 1, st);
+        if (e == cudaSuccess) e = launch_cost(p, &raw, 1, s.status, st);
         if (e == cudaSuccess) e = launch_block_cost(p, &pair, 1, st);
     } else if (e == cudaSuccess) {
-        e = launch_cost(p, &pair, 1, st);
+        e = launch_cost(p, &pair, 1, s.status, st);
     }
     if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_COST, true, st);
     if (e != cudaSuccess) return cuda_fail(h, e);

@@ -106,7 +106,7 @@ cudaError_t enqueue_class(simsense_batch* b, const BatchClass& c, cudaStream_t s
     const int n = (int)pp.size();
     const SelectDebug none{};
     cudaError_t e = launch_census(c.p, pp.data(), n, s);
-    if (e == cudaSuccess) e = launch_cost(c.p, pp.data(), n, s);
+    if (e == cudaSuccess) e = launch_cost(c.p, pp.data(), n, b->status, s);
     if (e == cudaSuccess) e = launch_paths(c.p, pp.data(), n, c.tune, s);
     if (e == cudaSuccess) e = launch_select(c.p, pp.data(), n, c.tune, none, b->status, s);
     return e;
