@@ -187,6 +187,62 @@ void mem_probe(int nsm)
     cudaFree(buf);
 }
 
+// warp-level (legacy) mma.sync rates: KIND 0 = m16n8k256 b1 and.popc,
+// 1 = m16n8k32 e4m3 -> f32, 2 = m16n8k16 f16 -> f32.  VARY: the A operand
+// changes every iteration, so a conversion of the operands cannot be hoisted
+// out of the loop (with fixed operands it can, and the rate then says
+// nothing about a kernel whose operands come from memory).
+template <int KIND, bool VARY>
+__global__ void __launch_bounds__(512) mma_kern(uint32_t* out, long long* cyc, int iters)
+{
+    uint32_t a0 = threadIdx.x * 0x9e3779b9u, a1 = a0 ^ 0x5555u, a2 = a0 * 3u, a3 = a1 * 5u, b0 = a0 + 7u, b1 = a1 + 9u;
+    const uint32_t m = KIND == 0 ? 0xFFFFFFFFu : 0x3c3c3c3cu;   // finite e4m3 / f16 bit patterns
+    a0 &= m; a1 &= m; a2 &= m; a3 &= m; b0 &= m; b1 &= m;
+    int c[4][4] = {};
+    float f[4][4] = {};
+    const long long t0 = clock64();
+    for (int i = 0; i < iters; i++) {
+        if (VARY) a0 = (a0 ^ ((uint32_t)i & 0x04040404u)) & m;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (KIND == 0)
+                asm volatile("mma.sync.aligned.m16n8k256.row.col.s32.b1.b1.s32.and.popc {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                             : "+r"(c[j][0]), "+r"(c[j][1]), "+r"(c[j][2]), "+r"(c[j][3])
+                             : "r"(a0), "r"(a1), "r"(a2 + j), "r"(a3), "r"(b0), "r"(b1));
+            else if (KIND == 1)
+                asm volatile("mma.sync.aligned.m16n8k32.row.col.f32.e4m3.e4m3.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                             : "+f"(f[j][0]), "+f"(f[j][1]), "+f"(f[j][2]), "+f"(f[j][3])
+                             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+            else
+                asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+                             : "+f"(f[j][0]), "+f"(f[j][1]), "+f"(f[j][2]), "+f"(f[j][3])
+                             : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+    }
+    const long long t1 = clock64();
+    int sum = 0;
+    for (int j = 0; j < 4; j++) sum += c[j][0] + c[j][1] + c[j][2] + c[j][3] + (int)(f[j][0] + f[j][1] + f[j][2] + f[j][3]);
+    out[blockIdx.x * blockDim.x + threadIdx.x] = (uint32_t)sum;
+    if (threadIdx.x == 0) cyc[blockIdx.x] = t1 - t0;
+}
+
+template <int KIND, bool VARY>
+static void run_mma(const char* name, int nsm, uint32_t* out, long long* cyc, double flops_per_mma)
+{
+    const int iters = 4096;
+    mma_kern<KIND, VARY><<<nsm, 512>>>(out, cyc, iters);
+    mma_kern<KIND, VARY><<<nsm, 512>>>(out, cyc, iters);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { printf("%s: error %s\n", name, cudaGetErrorString(e)); return; }
+    long long h[1024];
+    cudaMemcpy(h, cyc, nsm * sizeof(long long), cudaMemcpyDeviceToHost);
+    long long mx = 0;
+    for (int i = 0; i < nsm; i++) mx = h[i] > mx ? h[i] : mx;
+    const double per_clk = 16.0 * iters * 4 / (double)mx;      // 16 warps x iters x 4 per SM
+    printf("%-34s %6.3f warp-mma/clk/SM  %8.1f T op/s at 2.07 GHz\n", name, per_clk,
+           per_clk * flops_per_mma * nsm * 2.07e9 / 1e12);
+}
+
 int main()
 {
     int nsm = 0;
@@ -252,6 +308,14 @@ int main()
     lat<28>("vimin3.u16x2", out, cyc);
     lat<29>("viaddmin.u16x2", out, cyc);
     mem_probe(nsm);
+    if (nsm <= 1024) {
+        run_mma<0, false>("mma b1.and.popc m16n8k256", nsm, out, cyc, 16.0 * 8 * 256 * 2);
+        run_mma<0, true>("mma b1.and.popc m16n8k256, A varies", nsm, out, cyc, 16.0 * 8 * 256 * 2);
+        run_mma<1, false>("mma e4m3 m16n8k32", nsm, out, cyc, 16.0 * 8 * 32 * 2);
+        run_mma<1, true>("mma e4m3 m16n8k32, A varies", nsm, out, cyc, 16.0 * 8 * 32 * 2);
+        run_mma<2, false>("mma f16 m16n8k16", nsm, out, cyc, 16.0 * 8 * 16 * 2);
+        run_mma<2, true>("mma f16 m16n8k16, A varies", nsm, out, cyc, 16.0 * 8 * 16 * 2);
+    }
     cudaFree(out);
     cudaFree(cyc);
     return 0;

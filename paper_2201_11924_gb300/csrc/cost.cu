@@ -41,11 +41,11 @@
 //    two per register, so lane l of its warp holds d = s + l - 31.  One HFMA2
 //    leaves two results H in the low mantissa bytes of 1536 + H, one byte
 //    permute packs four consecutive s into a word, a funnel shift by the
-//    lane's offset (31 - l) mod 4 aligns it to four consecutive d, and the
-//    cells d >= D (255) and x - d < 0 (nbits) are masked in.  The words go to
-//    the pixel's staging row (pitch Dp + 16 spreads the lanes over the
-//    banks); the warp's 32 rows, 32 consecutive pixels and so a contiguous
-//    run of the volume, then go out as coalesced 16-byte stores.
+//    lane's offset (31 - l) mod 4 aligns it to four consecutive d in the
+//    pixel's staging row (pitch Dp + 16 spreads the lanes over the banks).
+//    The warp's 32 rows, 32 consecutive pixels and so a contiguous run of the
+//    volume, then go out as coalesced 16-byte stores, the cells d >= D (255)
+//    and x - d < 0 (nbits) rewritten in the chunks that have them.
 // Operand buffers, accumulators and their hand-offs are tracked by mbarriers
 // whose waits are all bounded: one that gives up records
 // SIMSENSE_ERR_TIMEOUT in the status word and makes every warp leave its loop
@@ -151,6 +151,22 @@ __device__ __forceinline__ void tmem_ld32h(uint32_t (&r)[16], uint32_t taddr)
                  : "r"(taddr));
 }
 
+// cells d0 .. d0 + 15 of pixel x: 255 for d >= D, nbits for x - d < 0
+__device__ __forceinline__ uint4 fix_chunk(uint4 v, int x, int d0, int D, int nbits)
+{
+    uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const int d = d0 + 4 * j;                       // bytes d .. d + 3 of word j
+        const int kx = x - d + 1, kd = D - d;           // bytes below each bound
+        const uint32_t keep_x = kx >= 4 ? 0xFFFFFFFFu : kx <= 0 ? 0u : 0xFFFFFFFFu >> (32 - 8 * kx);
+        const uint32_t keep_d = kd >= 4 ? 0xFFFFFFFFu : kd <= 0 ? 0u : 0xFFFFFFFFu >> (32 - 8 * kd);
+        w[j] = (w[j] & keep_x) | ((uint32_t)nbits * 0x01010101u & ~keep_x);
+        w[j] |= ~keep_d;
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
 template <int KS, int DP>
 struct TcShape {
     static constexpr int RB = 32 * KS;                  // expanded bytes per code (the K extent)
@@ -209,36 +225,21 @@ __device__ __forceinline__ uint32_t to_word(const uint32_t (&r)[16], int w, __ha
 }
 
 // stream word B (and B + 1) -> output word a = B - boff of the pixel's row
-// at base + 4 B; FX: bytes with d > x get nbits, FD: bytes with d >= D get 255.
-// B is a constant once the callers' loops unroll, which folds the range test
-// to the words at the two ends of the row.
-template <int DP, bool FX, bool FD>
-__device__ __forceinline__ void put_word(int B, uint32_t lo, uint32_t hi, uint32_t sh, int boff, uint32_t base, int x,
-                                         int D, uint32_t nb4)
+// at base + 4 B.  B is a constant once the callers' loops unroll, which folds
+// the range test to the words at the two ends of the row.
+template <int DP>
+__device__ __forceinline__ void put_word(int B, uint32_t lo, uint32_t hi, uint32_t sh, int boff, uint32_t base)
 {
     const int a = B - boff;
-    if ((B >= 7 || a >= 0) && (B < DP / 4 || a < DP / 4)) {
-        uint32_t v = __funnelshift_r(lo, hi, sh);
-        if (FX) {
-            const int k = x - 4 * a + 1;
-            const uint32_t keep = k >= 4 ? 0xFFFFFFFFu : k <= 0 ? 0u : 0xFFFFFFFFu >> (32 - 8 * k);
-            v = (v & keep) | (nb4 & ~keep);
-        }
-        if (FD) {
-            const int k = D - 4 * a;
-            v |= k >= 4 ? 0u : k <= 0 ? 0xFFFFFFFFu : ~(0xFFFFFFFFu >> (32 - 8 * k));
-        }
-        sts32(base + 4u * (uint32_t)B, v);
-    }
+    if ((B >= 7 || a >= 0) && (B < DP / 4 || a < DP / 4)) sts32(base + 4u * (uint32_t)B, __funnelshift_r(lo, hi, sh));
 }
 
 // one tile's row of this thread: TMEM chunks of 32 columns, loaded in
 // batches of up to 3 with one wait each (the accumulator is released after
 // the last batch), turned into words with one word carried across chunks
 // for the funnel shift
-template <int DP, bool FX, bool FD>
-__device__ __forceinline__ void row_to_staging(uint32_t taddr, uint32_t srow, int lane, __half2 bias, int x, int D,
-                                               uint32_t nb4, uint32_t acc_free)
+template <int DP>
+__device__ __forceinline__ void row_to_staging(uint32_t taddr, uint32_t srow, int lane, __half2 bias, uint32_t acc_free)
 {
     constexpr int NCH = DP / 32 + 1;                    // chunks: s < Dp + 32
     constexpr int NB = 3;                               // chunks per batch
@@ -266,9 +267,9 @@ __device__ __forceinline__ void row_to_staging(uint32_t taddr, uint32_t srow, in
                 uint32_t P[8];
 #pragma unroll
                 for (int w = 0; w < 8; w++) P[w] = to_word(r[k], w, mh, bias);
-                if (kk > 0) put_word<DP, FX, FD>(8 * kk - 1, carry, P[0], sh, boff, base, x, D, nb4);
+                if (kk > 0) put_word<DP>(8 * kk - 1, carry, P[0], sh, boff, base);
 #pragma unroll
-                for (int w = 0; w < 7; w++) put_word<DP, FX, FD>(8 * kk + w, P[w], P[w + 1], sh, boff, base, x, D, nb4);
+                for (int w = 0; w < 7; w++) put_word<DP>(8 * kk + w, P[w], P[w + 1], sh, boff, base);
                 carry = P[7];
             }
         }
@@ -418,7 +419,6 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
         const int g = warp >> 2, wq = warp & 3;
         const int m = 32 * wq + lane;                    // this thread's TMEM lane = pixel x0 + m
         const __half2 bias = __float2half2_rn(1536.0f + (float)((nbits + 1) >> 1));
-        const uint32_t nb4 = (uint32_t)nbits * 0x01010101u;
         const uint32_t srow = sS + (uint32_t)((g * kTileM + m) * S::SROW);
         TileMap::Pos q = tm.at(t0 < t1 ? t0 : 0);
         constexpr int CPP = DP / 16;                     // 16-byte chunks per pixel
@@ -432,13 +432,7 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
             if (*abort_flag) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t taddr = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(ab * S::TB + 96 - 32 * wq);
-            const int x = q.x0 + m;
-            const bool fx = q.x0 < DP - 1, fd = D < DP;
-            const uint32_t fr = acc_free + 8 * g;
-            if (!fx && !fd) row_to_staging<DP, false, false>(taddr, srow, lane, bias, x, D, nb4, fr);
-            else if (!fx) row_to_staging<DP, false, true>(taddr, srow, lane, bias, x, D, nb4, fr);
-            else if (!fd) row_to_staging<DP, true, false>(taddr, srow, lane, bias, x, D, nb4, fr);
-            else row_to_staging<DP, true, true>(taddr, srow, lane, bias, x, D, nb4, fr);
+            row_to_staging<DP>(taddr, srow, lane, bias, acc_free + 8 * g);
             __syncwarp();
             // the warp's 32 rows are 32 consecutive pixels: a contiguous run of
             // 32 Dp bytes, copied with 512 contiguous bytes per instruction
@@ -449,7 +443,12 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
 #pragma unroll 4
             for (int k = lane; k < 32 * CPP; k += 32) {
                 const int rr = k / CPP, cc = k - rr * CPP;
-                if (rr < nrow) *reinterpret_cast<uint4*>(dst + (size_t)k * 16) = lds128(wrow + rr * S::SROW + 16 * cc);
+                if (rr < nrow) {
+                    uint4 v = lds128(wrow + rr * S::SROW + 16 * cc);
+                    // cells d >= D (255) and x - d < 0 (nbits) of this chunk
+                    if (16 * cc + 16 > D || 16 * cc + 15 > xw + rr) v = fix_chunk(v, xw + rr, 16 * cc, D, nbits);
+                    *reinterpret_cast<uint4*>(dst + (size_t)k * 16) = v;
+                }
             }
             __syncwarp();
         }
