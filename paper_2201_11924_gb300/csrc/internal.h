@@ -98,7 +98,8 @@ struct Tuning {
 };
 
 // Raises a kernel's dynamic shared-memory limit to `bytes` when a launch needs
-// more than any earlier launch of that kernel on the current device.
+// more than any earlier launch of that kernel on the current device, and on
+// its first call asks for the largest shared-memory carve-out.
 cudaError_t ensure_smem(const void* kernel, size_t bytes);
 
 // Optional outputs of the selection kernel (device pointers, may be null).
