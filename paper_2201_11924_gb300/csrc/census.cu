@@ -96,6 +96,163 @@ census_kernel(PairTable<N> pt, int W, int H, int ww_rt, int wh_rt)
     else out[(size_t)y * W + x] = lo;
 }
 
+// The unrolled windows (5x5, 7x7, 9x7) four pixels per thread, four
+// comparisons per instruction sequence: byte j of a 32-bit word belongs to
+// pixel x + j, so one word holds one window offset's neighbours of the four
+// pixels.  For unsigned bytes a < b per byte: with d = (a | 0x80..) -
+// (b & 0x7f..) no borrow crosses a byte, bit 7 of d is [low7(a) >= low7(b)],
+// and a < b = (~a7 & b7) | (~(a7 ^ b7) & ~d7) -- one three-input logic op on
+// the top bits.  Offsets go in reverse raster order into byte-wise shift
+// registers (A = A >> 1 | lt & 0x80..: after eight offsets byte j of A holds
+// eight bits of pixel j), which leaves bit b of the code on offset
+// nbits - 1 - b, the MSB-first raster order of the one-pixel kernel above.
+constexpr int kSwTX = 32;                   // threads per block row, 4 pixels each
+constexpr int kSwTY = 8;                    // block rows
+constexpr int kSwPix = 4 * kSwTX;           // pixels per block row
+constexpr int kSwPad = 4;                   // tile bytes left of the block's first pixel (>= rx, word aligned)
+constexpr int kSwRow = kSwPix + 2 * kSwPad; // tile bytes per row (34 words)
+
+__device__ __forceinline__ uint32_t lt4(uint32_t a, uint32_t b, uint32_t d)
+{
+    return (~a & b) | (~(a ^ b) & ~d);      // valid in bits 7, 15, 23, 31
+}
+
+// tile words w and w + 1 from byte offset sh (0..3) on: bytes 4w + sh .. 4w + sh + 3
+template <int SH>
+__device__ __forceinline__ uint32_t word_at(const uint32_t* row, int w)
+{
+    if constexpr (SH == 0) return row[w];
+    else return __funnelshift_r(row[w], row[w + 1], 8 * SH);
+}
+
+template <typename CodeT, int WW, int WH, bool CS, int N>
+__global__ void __launch_bounds__(kSwTX * kSwTY)
+census_swar_kernel(PairTable<N> pt, int W, int H)
+{
+    constexpr int rx = WW / 2, ry = WH / 2;
+    constexpr int TH = kSwTY + 2 * ry;
+    constexpr int RW = kSwRow / 4;                       // words per tile row
+    constexpr int NB = CS ? (WW * WH - 1) / 2 : WW * WH - 1;
+    constexpr int NG = (NB + 7) / 8;                     // byte groups of the code
+    static_assert(rx <= kSwPad && NG <= 8 && NB <= 8 * (int)sizeof(CodeT), "window");
+    __shared__ __align__(16) uint32_t tile[TH * RW];
+    __shared__ __align__(16) uint32_t tile0[CS ? TH * RW : 1];
+    const int pair = blockIdx.z >> 1;
+    const uint8_t* img = (blockIdx.z & 1) ? pt.p[pair].right : pt.p[pair].left;
+    CodeT* out = static_cast<CodeT*>((blockIdx.z & 1) ? pt.p[pair].codes_right : pt.p[pair].codes_left);
+    const int gx0 = blockIdx.x * kSwPix - kSwPad, gy0 = blockIdx.y * kSwTY - ry;
+    // staged a word at a time when the rows are word aligned (W a multiple of
+    // 4 and the image 4-byte aligned), byte by byte otherwise; outside the
+    // image 255 (and 0 in the second tile)
+    const bool words = (W & 3) == 0 && (reinterpret_cast<uintptr_t>(img) & 3) == 0;
+    for (int i = threadIdx.y * kSwTX + threadIdx.x; i < TH * RW; i += kSwTX * kSwTY) {
+        const int w = i % RW, ty = i / RW;
+        const int gx = gx0 + 4 * w, gy = gy0 + ty;
+        uint32_t v = 0xffffffffu, v0 = 0u;
+        if (gy >= 0 && gy < H) {
+            const uint8_t* row = img + (size_t)gy * W;
+            if (words && gx >= 0 && gx + 3 < W) {
+                v = v0 = *reinterpret_cast<const uint32_t*>(row + gx);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    if (gx + j >= 0 && gx + j < W) {
+                        const uint32_t b = row[gx + j];
+                        v = (v & ~(0xffu << (8 * j))) | (b << (8 * j));
+                        v0 |= b << (8 * j);
+                    }
+                }
+            }
+        }
+        tile[i] = v;
+        if constexpr (CS) tile0[i] = v0;
+    }
+    __syncthreads();
+    const int x = blockIdx.x * kSwPix + 4 * threadIdx.x, y = blockIdx.y * kSwTY + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const uint32_t* trow = tile + threadIdx.y * RW + threadIdx.x;   // + dy * RW: window row dy
+    const uint32_t* t0row = CS ? tile0 + threadIdx.y * RW + threadIdx.x : trow;
+    constexpr uint32_t H7 = 0x80808080u;
+    const uint32_t c4 = trow[ry * RW + 1];               // the four centres
+    const uint32_t cm = c4 & ~H7;
+    uint32_t A[NG];
+#pragma unroll
+    for (int g = 0; g < NG; g++) A[g] = 0;
+    int f = 0;                                           // offsets fed so far (a constant once unrolled)
+#pragma unroll
+    for (int k = WW * WH - 1; k >= 0; k--) {             // reverse raster order
+        const int dy = k / WW, dx = k % WW;
+        if (dy == ry && dx == rx) continue;
+        if (CS && (dy > ry || (dy == ry && dx > rx))) continue;
+        // pixel x + j + dx - rx sits at tile byte 4 tx + kSwPad + j + dx - rx
+        const int b0 = kSwPad - rx + dx;
+        uint32_t a;
+        switch (b0 & 3) {
+            case 0: a = word_at<0>(trow + dy * RW, b0 >> 2); break;
+            case 1: a = word_at<1>(trow + dy * RW, b0 >> 2); break;
+            case 2: a = word_at<2>(trow + dy * RW, b0 >> 2); break;
+            default: a = word_at<3>(trow + dy * RW, b0 >> 2); break;
+        }
+        uint32_t lt;
+        if constexpr (CS) {
+            // the pair's second pixel p - o, read from the tile staged with 0
+            const int b1 = kSwPad - rx + (WW - 1 - dx);
+            const uint32_t* r0 = t0row + (WH - 1 - dy) * RW;
+            uint32_t b;
+            switch (b1 & 3) {
+                case 0: b = word_at<0>(r0, b1 >> 2); break;
+                case 1: b = word_at<1>(r0, b1 >> 2); break;
+                case 2: b = word_at<2>(r0, b1 >> 2); break;
+                default: b = word_at<3>(r0, b1 >> 2); break;
+            }
+            lt = lt4(a, b, (a | H7) - (b & ~H7));
+        } else {
+            lt = lt4(a, c4, (a | H7) - cm);
+        }
+        A[f >> 3] = (A[f >> 3] >> 1) | (lt & H7);
+        f++;
+    }
+    if constexpr (NB % 8 != 0) A[NG - 1] >>= 8 - NB % 8;
+    // byte j of A[g] is byte g of pixel j's code: a 4 x 4 byte transpose per
+    // four groups
+    uint32_t lo[4], hi[4] = {0u, 0u, 0u, 0u};
+    {
+        const uint32_t a0 = A[0], a1 = NG > 1 ? A[1] : 0u, a2 = NG > 2 ? A[2] : 0u, a3 = NG > 3 ? A[3] : 0u;
+        const uint32_t s0 = __byte_perm(a0, a1, 0x5140), s1 = __byte_perm(a0, a1, 0x7362);
+        const uint32_t s2 = __byte_perm(a2, a3, 0x5140), s3 = __byte_perm(a2, a3, 0x7362);
+        lo[0] = __byte_perm(s0, s2, 0x5410);
+        lo[1] = __byte_perm(s0, s2, 0x7632);
+        lo[2] = __byte_perm(s1, s3, 0x5410);
+        lo[3] = __byte_perm(s1, s3, 0x7632);
+    }
+    if constexpr (NG > 4) {
+        const uint32_t a0 = A[4], a1 = NG > 5 ? A[5] : 0u, a2 = NG > 6 ? A[6] : 0u, a3 = NG > 7 ? A[7] : 0u;
+        const uint32_t s0 = __byte_perm(a0, a1, 0x5140), s1 = __byte_perm(a0, a1, 0x7362);
+        const uint32_t s2 = __byte_perm(a2, a3, 0x5140), s3 = __byte_perm(a2, a3, 0x7362);
+        hi[0] = __byte_perm(s0, s2, 0x5410);
+        hi[1] = __byte_perm(s0, s2, 0x7632);
+        hi[2] = __byte_perm(s1, s3, 0x5410);
+        hi[3] = __byte_perm(s1, s3, 0x7632);
+    }
+    CodeT* o = out + (size_t)y * W + x;
+    if ((W & 3) == 0 && x + 3 < W) {                     // 16-byte aligned
+        if constexpr (sizeof(CodeT) == 8) {
+            reinterpret_cast<uint4*>(o)[0] = make_uint4(lo[0], hi[0], lo[1], hi[1]);
+            reinterpret_cast<uint4*>(o)[1] = make_uint4(lo[2], hi[2], lo[3], hi[3]);
+        } else {
+            *reinterpret_cast<uint4*>(o) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (x + j < W) {
+                if constexpr (sizeof(CodeT) == 8) o[j] = ((uint64_t)hi[j] << 32) | lo[j];
+                else o[j] = (CodeT)lo[j];
+            }
+        }
+    }
+}
+
 __global__ void widen_kernel(const uint32_t* __restrict__ in, uint64_t* __restrict__ out, size_t n)
 {
     size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -109,15 +266,18 @@ cudaError_t census_launch(const Params& p, const PairTable<N>& pt, int n, cudaSt
     dim3 grid((p.W + kTX - 1) / kTX, (p.H + kTY - 1) / kTY, 2 * n);
     const int w = p.win_w, h = p.win_h;
     // the unrolled 7x7 and 9x7 windows: 48 / 62 bits (64-bit codes) for the
-    // full census, 24 / 31 bits (32-bit codes) for the centre-symmetric one
+    // full census, 24 / 31 bits (32-bit codes) for the centre-symmetric one;
+    // 5x5: 24 / 12 bits
+    dim3 sblock(kSwTX, kSwTY);
+    dim3 sgrid((p.W + kSwPix - 1) / kSwPix, (p.H + kSwTY - 1) / kSwTY, 2 * n);
     if (w == 7 && h == 7 && p.wide_codes == !CS)
-        census_kernel<typename std::conditional<CS, uint32_t, uint64_t>::type, 7, 7, CS, N>
-            <<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
+        census_swar_kernel<typename std::conditional<CS, uint32_t, uint64_t>::type, 7, 7, CS, N>
+            <<<sgrid, sblock, 0, s>>>(pt, p.W, p.H);
     else if (w == 9 && h == 7 && p.wide_codes == !CS)
-        census_kernel<typename std::conditional<CS, uint32_t, uint64_t>::type, 9, 7, CS, N>
-            <<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
+        census_swar_kernel<typename std::conditional<CS, uint32_t, uint64_t>::type, 9, 7, CS, N>
+            <<<sgrid, sblock, 0, s>>>(pt, p.W, p.H);
     else if (w == 5 && h == 5 && !p.wide_codes)
-        census_kernel<uint32_t, 5, 5, CS, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
+        census_swar_kernel<uint32_t, 5, 5, CS, N><<<sgrid, sblock, 0, s>>>(pt, p.W, p.H);
     else if (p.wide_codes)
         census_kernel<uint64_t, 0, 0, CS, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
     else
