@@ -96,12 +96,14 @@ __device__ __forceinline__ uint32_t group_min(uint32_t v)
 
 // One pixel of the row for one lane group: sum, winner, uniqueness, offers to
 // the right view, parabola.  src is the pixel's first path in the stage.
-// DFULL: D equals the padded range, so every cell is a real disparity.
+// DFULL: D equals the padded range, so every cell is a real disparity;
+// otherwise `pad` marks the lane's padded cells (0xffff halves of the
+// even / odd cell words).
 template <int NP, int G, int PATHS, bool DFULL>
 __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act, int y, int W, int D,
                                              int uniq, uint32_t umagic, int subpixel, int gl,
                                              uint16_t* sw, uint32_t* keyR, uint32_t* info, uint32_t* fit,
-                                             const SelectDebug& dbg)
+                                             const SelectDebug& dbg, const uint32_t (&pad)[2 * ((NP + 1) / 2)])
 {
     constexpr int DPT = 2 * NP;
     constexpr int Dp = G * DPT;
@@ -129,6 +131,17 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
             od[k] += __byte_perm(a[k], 0, 0x4341) + __byte_perm(b[k], 0, 0x4341);
         }
     }
+    // padded cells d >= D (their path bytes carry no meaning) read as
+    // S = 0xffff: their keys lose to every real cell's (S <= 2040), in the
+    // winner, in the right-view minimum (d = 0 is real for every right
+    // pixel) and, with T capped at 0xffff below, in the uniqueness test
+    if (!DFULL) {
+#pragma unroll
+        for (int k = 0; k < NW; k++) {
+            ev[k] |= pad[2 * k];
+            od[k] |= pad[2 * k + 1];
+        }
+    }
     // cell j of the lane (d = d0 + j): word j/4, parity j%2, half (j/2)%2
     uint32_t S[DPT];
 #pragma unroll
@@ -142,7 +155,7 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
 #pragma unroll
     for (int j = 0; j < DPT; j++) {
         key[j] = (S[j] << 9) + (uint32_t)(d0 + j);
-        if (DFULL || d0 + j < D) kmin = min(kmin, key[j]);
+        kmin = min(kmin, key[j]);
     }
     kmin = group_min<G>(kmin);
     const int ds = (int)(kmin & 511u);
@@ -155,12 +168,13 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
     bool bad = false;
     if (uniq > 0) {
         const uint32_t num = 100u * smin + (uint32_t)(99 - uniq);
-        const uint32_t T = uniq == 99 ? num : __umulhi(num, umagic);
+        // capped at 0xffff: every real S is below it, a padded cell equals it
+        const uint32_t T = min(uniq == 99 ? num : __umulhi(num, umagic), 0xffffu);
         uint32_t m = 0xffffffffu;
 #pragma unroll
         for (int j = 0; j < DPT; j++) {
             const int d = d0 + j;
-            if ((uint32_t)(d - ds + 1) > 2u && (DFULL || d < D)) m = min(m, S[j]);
+            if ((uint32_t)(d - ds + 1) > 2u) m = min(m, S[j]);
         }
         bad = m < T;
     }
@@ -180,12 +194,12 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
         if (x >= Dp - 1) {                     // every cell maps inside the image
 #pragma unroll
             for (int j = 0; j < DPT; j++)
-                if (DFULL || d0 + j < D) atomicMin(&keyR[kr(x - d0 - j)], key[j]);
+                atomicMin(&keyR[kr(x - d0 - j)], key[j]);
         } else {
 #pragma unroll
             for (int j = 0; j < DPT; j++) {
                 const int d = d0 + j;
-                if ((DFULL || d < D) && d <= x) atomicMin(&keyR[kr(x - d)], key[j]);
+                if (d <= x) atomicMin(&keyR[kr(x - d)], key[j]);
             }
         }
         if (dbg.aggregated) {
@@ -241,6 +255,17 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, ui
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gl = lane % G, sub = lane / G;
     const int slot_pix = warp * SPW + sub;      // this group's pixel within a stage
+    // the lane's padded cells (its disparity chunk as select_pixel takes it)
+    uint32_t pad[2 * ((NP + 1) / 2)];
+    {
+        const int chunk = G == 16 ? (gl + 8 * ((threadIdx.x & 31) / 16)) % 16 : gl;
+        const int d0 = chunk * DPT;
+#pragma unroll
+        for (int k = 0; k < (NP + 1) / 2; k++) {
+            pad[2 * k] = (d0 + 4 * k >= D ? 0xffffu : 0u) | (d0 + 4 * k + 2 >= D ? 0xffff0000u : 0u);
+            pad[2 * k + 1] = (d0 + 4 * k + 1 >= D ? 0xffffu : 0u) | (d0 + 4 * k + 3 >= D ? 0xffff0000u : 0u);
+        }
+    }
     uint16_t* sw = sbuf + slot_pix * Dp;
     const int nst = (W + kPix - 1) / kPix;      // stages per row
     if (threadIdx.x == 0) {
@@ -273,10 +298,10 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, ui
             const uint8_t* src = ring + slot * stage_bytes + slot_pix * pbytes;
             if (D == Dp)
                 select_pixel<NP, G, PATHS, true>(src, x, x < W, y, W, D, uniq, umagic, subpixel, gl, sw, keyR,
-                                                 info, fit, dbg);
+                                                 info, fit, dbg, pad);
             else
                 select_pixel<NP, G, PATHS, false>(src, x, x < W, y, W, D, uniq, umagic, subpixel, gl, sw, keyR,
-                                                  info, fit, dbg);
+                                                  info, fit, dbg, pad);
             __syncthreads();                    // everyone is done with this slot
             if (abort_flag) {
                 if (threadIdx.x == 0) {
