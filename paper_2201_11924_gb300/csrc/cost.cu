@@ -440,6 +440,11 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
             const int nrow = tm.W - xw < 32 ? tm.W - xw : 32;
             uint8_t* dst = pt.p[q.pair].cost + ((size_t)q.y * tm.W + xw) * DP;
             const uint32_t wrow = srow - (uint32_t)(lane * S::SROW);
+            // the volume is read next by every path: kept in L2 ahead of
+            // other lines where it fits (measured 4 us less path time at
+            // 1280 x 720, D = 128, whose 118 MB volume fits the 129 MB L2)
+            uint64_t keep;
+            asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(keep));
 #pragma unroll 4
             for (int k = lane; k < 32 * CPP; k += 32) {
                 const int rr = k / CPP, cc = k - rr * CPP;
@@ -447,7 +452,9 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
                     uint4 v = lds128(wrow + rr * S::SROW + 16 * cc);
                     // cells d >= D (255) and x - d < 0 (nbits) of this chunk
                     if (16 * cc + 16 > D || 16 * cc + 15 > xw + rr) v = fix_chunk(v, xw + rr, 16 * cc, D, nbits);
-                    *reinterpret_cast<uint4*>(dst + (size_t)k * 16) = v;
+                    asm volatile("st.global.L2::cache_hint.v4.u32 [%0], {%1,%2,%3,%4}, %5;"
+                                 ::"l"(dst + (size_t)k * 16), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "l"(keep)
+                                 : "memory");
                 }
             }
             __syncwarp();
