@@ -13,7 +13,7 @@
 // -1), the Hamming distance of two n-bit codes is (n - sum_k sL_k sR_k) / 2.
 // For one image row the cost volume is therefore a band of the product of the
 // left codes (pixels x bits) and the transposed right codes, a contraction
-// the fifth-generation tensor cores run in e4m3 (+-1.0 exactly) with an f32
+// the fifth-generation tensor cores run in e4m3 (+-1.0 exactly) with an f16
 // accumulator (every partial sum is an integer of magnitude <= 64, exact).
 // POPC, the alternative, issues 16 results per clock per SM on this GPU, two
 // per cell for codes above 32 bits; here one tcgen05.mma per 32 code bits
@@ -44,7 +44,8 @@
 //    lane's offset (31 - l) mod 4 aligns it to four consecutive d in the
 //    pixel's staging row (pitch Dp + 16 spreads the lanes over the banks).
 //    The warp's 32 rows, 32 consecutive pixels and so a contiguous run of the
-//    volume, then go out as coalesced 16-byte stores, the cells d >= D (255)
+//    volume, then go out as coalesced 16-byte stores (with an L2 evict-last
+//    policy: the path kernel reads the volume next), the cells d >= D (255)
 //    and x - d < 0 (nbits) rewritten in the chunks that have them.
 // Operand buffers, accumulators and their hand-offs are tracked by mbarriers
 // whose waits are all bounded: one that gives up records
