@@ -98,6 +98,17 @@ typedef struct simsense_ctx* simsense_t;
 #define SIMSENSE_OPT_BLOCK          4
 #define SIMSENSE_OPT_MEDIAN         5
 
+/*
+ * SIMSENSE_OPT_TEST_STALL (value 0/1, default 0): a test of the bounded
+ * device-side waits.  While 1, the cost stage's MMA-issuing thread issues no
+ * tensor-core work, so the waits on its completions run out (each after a
+ * limit of 2048 short tries instead of the normal ~1 s): the stage gives up,
+ * frees its tensor memory and returns, simsense_device_status then reports
+ * SIMSENSE_ERR_TIMEOUT, the depth of that call is undefined, and the handle
+ * and the CUDA context stay usable.  Nothing faults, traps or hangs.
+ */
+#define SIMSENSE_OPT_TEST_STALL     6
+
 /* stages timed under SIMSENSE_OPT_PROFILE, in launch order */
 #define SIMSENSE_STAGE_CENSUS       0     /* census transform of both views */
 #define SIMSENSE_STAGE_COST         1     /* Hamming matching cost volume */

@@ -70,6 +70,7 @@ constexpr uint32_t kOne4 = 0x38383838u;     // four e4m3 +1.0
 constexpr uint32_t kSign4 = 0x80808080u;    // their sign bits
 constexpr uint32_t kSpread = 0x10204080u;   // nibble bit i -> bit 8 i + 7
 constexpr uint32_t kMaxTries = 1u << 20;    // bound on the tries of one mbarrier wait
+constexpr uint32_t kStallTries = 1u << 11;  // the same under the wait test (SIMSENSE_OPT_TEST_STALL)
 constexpr uint32_t kSuspendNs = 1000;       // suspend-time hint of one try
 
 // per 4-byte group j of an expanded left code: 0xFF for the bytes below nbits
@@ -129,9 +130,9 @@ __device__ __forceinline__ void bar_arrive(uint32_t bar)
 
 // try_wait suspends the waiting warp (up to the hint, in ns) instead of
 // spinning, so waiting warps leave the issue slots to the working ones
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity)
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, uint32_t tries)
 {
-    for (uint32_t it = 0; it < kMaxTries; it++) {
+    for (uint32_t it = 0; it < tries; it++) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(bar), "r"(parity), "r"(kSuspendNs) : "memory");
@@ -304,7 +305,8 @@ __device__ __forceinline__ CodeT load_code(const CodeT* row, int x, int W)
 // blockIdx.x takes tiles [t0, t1) of ntiles = pairs x rows x ceil(W / 128).
 template <int KS, int DP, int N>
 __global__ void __launch_bounds__(kCostThreads, 1)
-cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km, int* __restrict__ status)
+cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km, int* __restrict__ status,
+            int stall)
 {
     using CodeT = typename std::conditional<KS == 2, uint64_t, uint32_t>::type;
     using S = TcShape<KS, DP>;
@@ -318,6 +320,7 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
     volatile int* abort_flag = reinterpret_cast<volatile int*>(cost_smem + S::BAR_OFF + 68);
     // the block's tiles [t0, t1), walked in order by every role
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t tries = stall ? kStallTries : kMaxTries;
     const int t0 = (int)(((long long)blockIdx.x * ntiles) / gridDim.x);
     const int t1 = (int)(((long long)(blockIdx.x + 1) * ntiles) / gridDim.x);
 
@@ -363,7 +366,7 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
                 tm.step(q);
                 fetch(q, nl, nr);
             }
-            if (i >= 2 && !bar_wait(ops_free + 8 * b, ((i - 2) >> 1) & 1)) {
+            if (i >= 2 && !bar_wait(ops_free + 8 * b, ((i - 2) >> 1) & 1, tries)) {
                 if (status) atomicExch(status, SIMSENSE_ERR_TIMEOUT);
                 *abort_flag = 1;
             }
@@ -387,16 +390,17 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
             int last = -1;
             for (int t = t0, i = 0; t < t1; t++, i++) {
                 const int b = i & 1, ab = i % S::NBUF;
-                bool ok = bar_wait(ops_full + 8 * b, (i >> 1) & 1);
+                bool ok = bar_wait(ops_full + 8 * b, (i >> 1) & 1, tries);
                 // the accumulator's previous tile has been read (the mbarriers
                 // go by tile parity, the epilogue group, whatever NBUF is, so
                 // that no wait is ever a phase ahead of its barrier)
-                if (ok && i >= S::NBUF) ok = bar_wait(acc_free + 8 * ((i - S::NBUF) & 1), ((i - S::NBUF) >> 1) & 1);
+                if (ok && i >= S::NBUF) ok = bar_wait(acc_free + 8 * ((i - S::NBUF) & 1), ((i - S::NBUF) >> 1) & 1, tries);
                 if (!ok) {
                     if (status) atomicExch(status, SIMSENSE_ERR_TIMEOUT);
                     *abort_flag = 1;
                 }
                 if (*abort_flag) break;
+                if (stall) continue;                    // the wait test: nothing completes
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sA = sbase + b * S::OPS, sB = sA + kTileM * S::RB;
                 const uint32_t d = tmem + (uint32_t)(ab * S::TB);
@@ -412,7 +416,7 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
                 mma_commit(acc_full + 8 * b);           // the accumulator is ready for group b
                 last = i;
             }
-            if (last >= 0) bar_wait(acc_full + 8 * (last & 1), (last >> 1) & 1);   // no MMA in flight
+            if (last >= 0) bar_wait(acc_full + 8 * (last & 1), (last >> 1) & 1, kMaxTries);   // no MMA in flight
         }
         __syncwarp();
     } else {
@@ -426,7 +430,7 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
         for (int t = t0, i = 0; t < t1; t++, i++, tm.step(q)) {
             if ((i & 1) != g) continue;
             const int ab = S::NBUF == 2 ? g : 0;
-            if (!bar_wait(acc_full + 8 * g, (uint32_t)(i >> 1) & 1u)) {
+            if (!bar_wait(acc_full + 8 * g, (uint32_t)(i >> 1) & 1u, tries)) {
                 if (status) atomicExch(status, SIMSENSE_ERR_TIMEOUT);
                 *abort_flag = 1;
             }
@@ -497,7 +501,7 @@ cudaError_t cost_launch(const Params& p, const PairTable<N>& pt, int n, int* sta
     TileMap tm{p.W, p.H, (p.W + kTileM - 1) / kTileM};
     const int ntiles = n * p.H * tm.tx;
     const int grid = ntiles < sm_count() ? ntiles : sm_count();
-    kernel<<<grid, kCostThreads, S::SMEM, s>>>(pt, tm, ntiles, p.D, p.nbits, km, status);
+    kernel<<<grid, kCostThreads, S::SMEM, s>>>(pt, tm, ntiles, p.D, p.nbits, km, status, p.test_stall);
     return cudaGetLastError();
 }
 template <int KS, int N>

@@ -32,6 +32,9 @@ struct Params {
     int census_cs = 0;
     int block_w = 1, block_h = 1;
     int median = 0;
+    // test of the bounded waits (SIMSENSE_OPT_TEST_STALL): the cost stage
+    // issues no MMAs and gives up after a short wait
+    int test_stall = 0;
 };
 
 // Applies a variant option to p (re-deriving nbits and the code width) after

@@ -310,6 +310,10 @@ int simsense_set_option(simsense_t h, int opt, int value)
         case SIMSENSE_OPT_BLOCK:
         case SIMSENSE_OPT_MEDIAN:
             return set_variant(h->p, opt, value);
+        case SIMSENSE_OPT_TEST_STALL:
+            if (value != 0 && value != 1) return SIMSENSE_ERR_INVALID_ARG;
+            h->p.test_stall = value;
+            return SIMSENSE_OK;
         default:
             return SIMSENSE_ERR_INVALID_ARG;
     }

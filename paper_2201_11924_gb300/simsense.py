@@ -24,6 +24,7 @@ OPT_PROFILE = 2
 OPT_CENSUS_CS = 3
 OPT_BLOCK = 4
 OPT_MEDIAN = 5
+OPT_TEST_STALL = 6      # test of the bounded device-side waits (see include/simsense.h)
 STAGES = ("census", "cost", "paths", "select")
 
 _lock = threading.Lock()
