@@ -5,6 +5,8 @@
 
 #include "internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace simsense;
 
 namespace {
@@ -54,9 +56,13 @@ void free_profile(ProfileRing& r)
     r = ProfileRing{};
 }
 
-// Records the start (end = false) or end of `stage` for the current call.
+// Records the start (end = false) or end of `stage` for the current call:
+// a named NVTX range on the host (seen by nsys / ncu, free without a tool)
+// and, with SIMSENSE_OPT_PROFILE, CUDA events on the stream.
 cudaError_t mark(simsense_ctx* h, int stage, bool end, cudaStream_t st)
 {
+    if (end) nvtxRangePop();
+    else nvtxRangePushA(simsense_stage_name(stage));
     ProfileRing& r = h->prof;
     if (!r.on || r.count >= ProfileRing::kSlots) return cudaSuccess;
     return cudaEventRecord(r.ev[r.count * 2 * SIMSENSE_NUM_STAGES + 2 * stage + (end ? 1 : 0)], st);
@@ -87,7 +93,10 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
     const Tuning tune{};
     e = mark(h, SIMSENSE_STAGE_CENSUS, false, st);
     if (e == cudaSuccess) e = launch_census(p, &pair, 1, st);
-    if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_CENSUS, true, st);
+    {
+        const cudaError_t e_end = mark(h, SIMSENSE_STAGE_CENSUS, true, st);   // pops the range in any case
+        if (e == cudaSuccess) e = e_end;
+    }
     if (e != cudaSuccess) return cuda_fail(h, e);
     e = mark(h, SIMSENSE_STAGE_COST, false, st);
     if (p.block_w > 1 || p.block_h > 1) {
@@ -100,11 +109,17 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
     } else if (e == cudaSuccess) {
         e = launch_cost(p, &pair, 1, s.status, st);
     }
-    if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_COST, true, st);
+    {
+        const cudaError_t e_end = mark(h, SIMSENSE_STAGE_COST, true, st);   // pops the range in any case
+        if (e == cudaSuccess) e = e_end;
+    }
     if (e != cudaSuccess) return cuda_fail(h, e);
     e = mark(h, SIMSENSE_STAGE_PATHS, false, st);
     if (e == cudaSuccess) e = launch_paths(p, &pair, 1, tune, st);
-    if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_PATHS, true, st);
+    {
+        const cudaError_t e_end = mark(h, SIMSENSE_STAGE_PATHS, true, st);   // pops the range in any case
+        if (e == cudaSuccess) e = e_end;
+    }
     if (e != cudaSuccess) return cuda_fail(h, e);
     SelectDebug sd{};
     if (dbg) {
@@ -124,7 +139,10 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
     } else if (e == cudaSuccess) {
         e = launch_select(p, &pair, 1, tune, sd, s.status, st);
     }
-    if (e == cudaSuccess) e = mark(h, SIMSENSE_STAGE_SELECT, true, st);
+    {
+        const cudaError_t e_end = mark(h, SIMSENSE_STAGE_SELECT, true, st);   // pops the range in any case
+        if (e == cudaSuccess) e = e_end;
+    }
     if (e != cudaSuccess) return cuda_fail(h, e);
     if (h->prof.on && h->prof.count < ProfileRing::kSlots) h->prof.count++;
     if (dbg && dbg->census_left) {
