@@ -84,11 +84,11 @@ def algorithmic_ops(wl):
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one
-# ncu capture (profiles/ncu_full_1280x720_D128_8path.md), with the SHA-1 of
-# the kernel's source at the time: a changed source reports null.
+# ncu capture (profiles/ncu_paths_dram_1280x720_D128_8path.md), with the SHA-1
+# of the kernel's source at the time: a changed source reports null.
 MEASURED_TRAFFIC = {
     "1280x720_D128_census7x7_8path": {
-        "paths": (536795136 + 887504384, "c92b81b5107b142f958ce668184dc6800818212b",
+        "paths": (548959488 + 887986944, "2cd60c748dcd15cde1c71e8d54def5e7648970c2",
                   "paper_2201_11924_gb300/csrc/sgm_paths.cu"),
     },
 }

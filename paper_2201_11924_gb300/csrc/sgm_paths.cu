@@ -211,7 +211,8 @@ template <int NQ, int G, int PF, bool Guard>
 __device__ __forceinline__ void walk_steps(int base, int n, int len, uint32_t ring, const uint8_t*& cf,
                                            long long cstep, uint8_t*& op, long long ostep,
                                            uint32_t (&Lc)[2 * NQ], uint32_t (&Lp)[2 * NQ], uint32_t& mm,
-                                           uint32_t p1, uint32_t p2, uint32_t edge_lo, uint32_t edge_hi)
+                                           uint32_t& cap, uint32_t p1, uint32_t p2, uint32_t edge_lo,
+                                           uint32_t edge_hi)
 {
 #pragma unroll
     for (int k = 0; k < PF; k++) {
@@ -229,9 +230,9 @@ __device__ __forceinline__ void walk_steps(int base, int n, int len, uint32_t ri
             const uint32_t Oprev = q == 0 ? o_below : Lp[2 * q - 1];
             const uint32_t Enext = q == NQ - 1 ? e_above : Lp[2 * q + 2];
             // E = (d0, d2): d + 1 is O = (d1, d3), d - 1 is (d-1, d1)
-            const uint32_t tE = vmin3(Lc[2 * q], Lp[2 * q + 1], shift_pair(Oprev, Lp[2 * q + 1]));
+            const uint32_t tE = vmin2(vmin3(Lc[2 * q], Lp[2 * q + 1], shift_pair(Oprev, Lp[2 * q + 1])), cap);
             // O = (d1, d3): d - 1 is E = (d0, d2), d + 1 is (d2, d4)
-            const uint32_t tO = vmin3(Lc[2 * q + 1], Lp[2 * q], shift_pair(Lp[2 * q], Enext));
+            const uint32_t tO = vmin2(vmin3(Lc[2 * q + 1], Lp[2 * q], shift_pair(Lp[2 * q], Enext)), cap);
             // cost bytes (c0, c1, c2, c3) -> (c0, c2) and (c1, c3)
             const uint32_t cE = cw[q] & 0x00ff00ffu;
             const uint32_t cO = __byte_perm(cw[q], 0, 0x4341);
@@ -245,10 +246,10 @@ __device__ __forceinline__ void walk_steps(int base, int n, int len, uint32_t ri
         cp_cost<NQ>(ring + k * 512, cf, Guard ? i + PF < len : true);
         cf += cstep;
         mm = group_min<NQ, G>(L);
-        const uint32_t cap = mm + p2;
+        cap = mm + p2;
 #pragma unroll
         for (int k2 = 0; k2 < 2 * NQ; k2++) {
-            Lc[k2] = vmin2(L[k2], cap);
+            Lc[k2] = L[k2];
             Lp[k2] = L[k2] + p1;
         }
     }
@@ -296,8 +297,10 @@ __device__ __forceinline__ void walk(const uint8_t* __restrict__ C, int W, int H
     }
     // State before the entry pixel: L' = 0 and m' = 0, which makes the
     // recurrence return exactly C there (the path's start condition).
-    // Lc = min(L', m' + P2) and Lp = L' + P1 per pair, E pairs at even and O
-    // pairs at odd indices.
+    // Lc = L' and Lp = L' + P1 per pair, E pairs at even and O pairs at odd
+    // indices; cap = m' + P2 is applied after the three-input minimum of
+    // L'(d) and L'(d -+ 1) + P1, which keeps it off the step-to-step chain
+    // (m' -> cap -> L -> m'): min is associative, the result is the same.
     uint32_t Lc[2 * NQ], Lp[2 * NQ];
 #pragma unroll
     for (int k = 0; k < 2 * NQ; k++) {
@@ -305,15 +308,16 @@ __device__ __forceinline__ void walk(const uint8_t* __restrict__ C, int W, int H
         Lp[k] = p1;
     }
     uint32_t mm = 0;
+    uint32_t cap = p2;                        // m' + P2, applied after the three-input minimum
 
     // steps whose pixel and prefetch target lie on every lane's scanline
     const int nmain = nmin > PF ? (nmin - PF) / PF * PF : 0;
     int base = 0;
     for (; base < nmain; base += PF)
-        walk_steps<NQ, G, PF, false>(base, n, len, ring, cf, cstep, op, ostep, Lc, Lp, mm, p1, p2,
+        walk_steps<NQ, G, PF, false>(base, n, len, ring, cf, cstep, op, ostep, Lc, Lp, mm, cap, p1, p2,
                                      edge_lo, edge_hi);
     for (; base < n; base += PF)
-        walk_steps<NQ, G, PF, true>(base, n, len, ring, cf, cstep, op, ostep, Lc, Lp, mm, p1, p2,
+        walk_steps<NQ, G, PF, true>(base, n, len, ring, cf, cstep, op, ostep, Lc, Lp, mm, cap, p1, p2,
                                     edge_lo, edge_hi);
 }
 
