@@ -171,3 +171,26 @@ def test_bad_tensor_arguments_raise(lib):
             m.compute(good[:, :32], good)
         with pytest.raises(ValueError):
             m.compute(good.cpu(), good)
+
+
+@pytest.mark.parametrize("W", [128, 130])
+def test_unaligned_image_pointers_give_the_same_depth(lib, W):
+    """Images that start at an odd byte address (the census stages its tile
+    byte by byte then, a word at a time otherwise) give bit-identical depth."""
+    import torch
+    wl = _small("odd_base", W, 40, 48, 7, 7, 8, 15, 1, True, seed=21)
+    p = scenes.make_pair(wl)
+    dev = torch.device("cuda:0")
+    n = wl.W * wl.H
+    with lib.SimSense.from_workload(wl) as m:
+        a = m.compute(torch.from_numpy(p["left"]).to(dev), torch.from_numpy(p["right"]).to(dev)).cpu().numpy()
+        lb = torch.zeros(n + 3, dtype=torch.uint8, device=dev)
+        rb = torch.zeros(n + 3, dtype=torch.uint8, device=dev)
+        lb[1:n + 1] = torch.from_numpy(p["left"]).to(dev).reshape(-1)
+        rb[3:n + 3] = torch.from_numpy(p["right"]).to(dev).reshape(-1)
+        lo, ro = lb[1:n + 1].view(wl.H, wl.W), rb[3:n + 3].view(wl.H, wl.W)
+        assert lo.data_ptr() % 4 == 1 and ro.data_ptr() % 4 == 3
+        b = m.compute(lo, ro).cpu().numpy()
+        torch.cuda.synchronize()
+        assert m.device_status() == 0
+    np.testing.assert_array_equal(a, b)
