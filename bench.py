@@ -6,7 +6,9 @@
 Prints ONE JSON line (rank 0).  ``value`` is device-timed whole-job
 throughput with the inputs resident in HBM; ``e2e`` is the same metric
 through the host-buffer C-ABI call (pinned host -> device copies, compute,
-depth copied back, every step); ``roofline`` reports the dominant kernel's
+depth copied back and read on the host, every step), with two frames in
+flight on two handles and streams as a camera stream runs it (the figure for
+one frame at a time is in the same object); ``roofline`` reports the dominant kernel's
 achieved integer-op rate (algorithmic ops / its CUDA-event duration) against
 the derived INT32 peak; ``cpu_baseline`` is the CPU oracle timed on a bounded
 sample on this host.  ``--impl reference`` times that oracle alone, on the
@@ -623,25 +625,46 @@ def main():
     el_ms = rep.max_over_ranks(el_ms, dev)
     value = world * args.steps / (el_ms / 1e3)
 
-    # end to end through the host-buffer call: pinned inputs in, depth out
+    # end to end through the host-buffer call, as a camera stream runs it: two
+    # frames in flight (two handles, each on its own stream); every frame
+    # uploads its own pinned inputs, computes and downloads its depth, and its
+    # result is read on the host before its handle takes the frame after next
     hl = [torch.from_numpy(p["left"]).pin_memory() for p in pairs]
     hr = [torch.from_numpy(p["right"]).pin_memory() for p in pairs]
-    hd = torch.empty((wl.H, wl.W), dtype=torch.float32).pin_memory()
+    hd = [torch.empty((wl.H, wl.W), dtype=torch.float32).pin_memory() for _ in range(2)]
+    m2 = simsense.SimSense.from_workload(wl)
+    hs = [m, m2]
+    ss = [stream, torch.cuda.Stream(device=dev)]
     for i in range(args.warmup):
-        m.compute_host(hl[i % n_pairs], hr[i % n_pairs], hd)
-        stream.synchronize()
+        hs[i % 2].compute_host(hl[i % n_pairs], hr[i % n_pairs], hd[i % 2], stream=ss[i % 2])
+    torch.cuda.synchronize()
     rep.barrier()
-    e2e_steps = max(3, min(args.steps, 500))
+    e2e_steps = max(4, min(args.steps, 500))
     t0 = time.perf_counter()
     for i in range(e2e_steps):
-        m.compute_host(hl[i % n_pairs], hr[i % n_pairs], hd)
-        stream.synchronize()
-        _ = float(hd[0, 0])
+        k = i % 2
+        if i >= 2:                               # frame i - 2 on this handle: done, read
+            ss[k].synchronize()
+            _ = float(hd[k][0, 0])
+        hs[k].compute_host(hl[i % n_pairs], hr[i % n_pairs], hd[k], stream=ss[k])
+    for k in range(2):
+        ss[k].synchronize()
+        _ = float(hd[k][0, 0])
     e2e_s = time.perf_counter() - t0
+    m2.close()
+    # the same with one frame in flight (each call waits for the previous)
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        m.compute_host(hl[i % n_pairs], hr[i % n_pairs], hd[0], stream=stream)
+        stream.synchronize()
+        _ = float(hd[0][0, 0])
+    e2e_one = time.perf_counter() - t0
     e2e_s = rep.max_over_ranks(e2e_s, dev)
+    e2e_one = rep.max_over_ranks(e2e_one, dev)
     e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": 2 * wl.W * wl.H, "d2h_bytes_per_step": 4 * wl.W * wl.H,
-           "steps": e2e_steps}
+           "steps": e2e_steps, "frames_in_flight": 2,
+           "one_in_flight_value": world * e2e_steps / e2e_one}
 
     # the batched form on the same workload: batch_pairs pairs per CUDA-graph launch
     batched = None
