@@ -32,17 +32,20 @@ _lib = None
 PATH_DIRS = [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, 1), (1, -1), (-1, -1)]
 
 
-def build(force: bool = False) -> str:
-    """Compile oracle.c into a shared library next to it (gcc, -O2)."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
-        return _LIB_PATH
-    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+def build(force: bool = False, src: str | None = None, out: str | None = None) -> str:
+    """Compile oracle.c (or ``src``, a copy of it) into a shared library next
+    to it (or at ``out``) with gcc -O2."""
+    src = src or _SRC
+    out = out or _LIB_PATH
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src):
+        return out
+    tmp = out + f".tmp{os.getpid()}.{threading.get_ident()}"
     # -ffp-contract=off: no fused multiply-adds, so the fp64 camera arithmetic
     # rounds after every operation as written
-    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-shared", "-fPIC", "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    os.replace(tmp, out)
+    return out
 
 
 def _load():

@@ -63,26 +63,36 @@ def test_half_pixel_shift_matches_library_bilinear():
 def test_radial_distortion_moves_points_by_the_polynomial():
     # on the x axis y = 0: x_d = x (1 + k1 x^2 + k2 x^4 + k3 x^6); a raw image
     # that is a ramp in x (value = raw column) reads back the distorted column
+    # (x reaches 1.5, where each of the three terms moves the point by more
+    # than a pixel)
     W, H = 64, 9
     ramp = np.tile(np.arange(W, dtype=np.uint8), (H, 1))
-    f, cx, cy = 40.0, 10.0, 4.0
-    k1, k2, k3 = 0.02, -0.001, 0.0001
+    f, cx, cy = 20.0, 4.0, 4.0
+    k1, k2, k3 = 0.05, -0.02, 0.01
     out = oracle.rectify(ramp, oracle.camera(f, f, cx, cy, k1=k1, k2=k2, k3=k3))
-    for u in (10, 15, 20, 25, 30):
+    for u in (10, 15, 20, 25, 30, 34):
         x = (u - cx) / f
         ur = f * x * (1 + k1 * x * x + k2 * x ** 4 + k3 * x ** 6) + cx
         assert abs(int(out[4, u]) - ur) <= 0.5 + 1.0 / 256, u
 
 
 def test_tangential_terms_are_symmetric_in_their_axes():
-    # p1 alone shifts v on the y axis as p1 (3 y^2); p2 alone shifts u on the x axis as p2 (3 x^2)
+    # Brown-Conrady on an axis: p1 alone shifts v on the y axis by p1 (3 y^2)
+    # and leaves u on the x axis alone; p2 alone does the same with the axes
+    # exchanged (shifts of 1-3 px here, well above the rounding)
     W, H = 40, 40
     rampx = np.tile(np.arange(W, dtype=np.uint8), (H, 1))
-    f, c, p = 30.0, 8.0, 0.01
-    out = oracle.rectify(rampx, oracle.camera(f, f, c, c, p2=p))
-    for u in (12, 18, 24):
-        x = (u - c) / f
-        assert abs(int(out[int(c), u]) - (f * (x + p * 3 * x * x) + c)) <= 0.5 + 1.0 / 256
+    rampy = rampx.T.copy()
+    f, c, p = 30.0, 8.0, 0.1
+    for p1, p2 in ((0.0, p), (p, 0.0)):
+        cam = oracle.camera(f, f, c, c, p1=p1, p2=p2)
+        outx, outy = oracle.rectify(rampx, cam), oracle.rectify(rampy, cam)
+        for t in (12, 18, 24):
+            x = (t - c) / f
+            # along the x axis (v = c) the column read moves by p2 (3 x^2) only
+            assert abs(int(outx[int(c), t]) - (f * (x + p2 * 3 * x * x) + c)) <= 0.5 + 1.0 / 256
+            # along the y axis (u = c) the row read moves by p1 (3 y^2) only
+            assert abs(int(outy[t, int(c)]) - (f * (x + p1 * 3 * x * x) + c)) <= 0.5 + 1.0 / 256
 
 
 def test_registration_identity_and_zbuffer():
@@ -110,3 +120,17 @@ def test_registration_translation_along_the_axis():
     # the plane shrinks by half about the principal point: columns 8..22 only
     cols = np.flatnonzero(filled.any(axis=0))
     assert cols.min() >= 7 and cols.max() <= 23 and filled.sum() == len(np.unique(np.floor((np.arange(31) - cx) / 2 + cx + 0.5))) * len(np.unique(np.floor((np.arange(21) - cy) / 2 + cy + 0.5)))
+
+
+@pytest.mark.parametrize("tx,ty", [(0.05, 0.0), (0.0, -0.075), (0.05, 0.025)])
+def test_registration_sideways_translation_shifts_the_image(tx, ty):
+    # the RGB camera sees the point X + t: on a fronto-parallel plane at Z
+    # every pixel moves by (f tx / Z, f ty / Z) = whole pixels here, with its
+    # depth unchanged
+    depth = np.full((21, 31), 2.0, dtype=np.float32)
+    f, cx, cy, Z = 80.0, 15.0, 10.0, 2.0
+    out = oracle.register(depth, f, f, cx, cy, f, f, cx, cy, np.eye(3), [tx, ty, 0.0], 31, 21)
+    sx, sy = int(round(f * tx / Z)), int(round(f * ty / Z))
+    want = np.zeros_like(depth)
+    want[max(sy, 0):21 + min(sy, 0), max(sx, 0):31 + min(sx, 0)] = Z
+    assert np.array_equal(out, want)

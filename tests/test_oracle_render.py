@@ -5,9 +5,12 @@ parameters are readings).
 
 Pins: the cosine-cubed falloff of a fronto-parallel Lambertian wall lit from
 the camera centre (closed form), the stereo shift d = f b / Z between the two
-views, projector shadows against an independent ray-sphere test, linearity of
-the mix in the transmission weight, and the specular highlight of a glossy
-metal sphere at the point facing the light."""
+views, projector shadows and nearest hits against an independent ray-sphere
+test, no shadow from behind the projector, Helmholtz reciprocity of the BSDF,
+linearity of the mix in the transmission weight, and the specular highlight of
+a glossy metal sphere at the point facing the light.  Not pinned by any of
+them: the constants of the named approximations (Schlick's exponent 5, the
+dielectric F0 = 0.04), which the oracle restates."""
 import numpy as np
 import pytest
 
@@ -54,13 +57,19 @@ def test_projector_shadow_of_a_sphere():
     wall = _wall(Z, albedo=albedo)
     ball = oracle.sphere(tuple(c), r, albedo=0.3)
     _, _, lf, _ = _render([wall, ball], pat, proj=tuple(proj), ambient=amb, gain=gain)
+    # the sphere alone: the wall lies behind it, so it neither hides nor shadows it
+    _, _, lf_ball, _ = _render([ball], pat, proj=tuple(proj), ambient=amb, gain=gain)
     us, vs = np.meshgrid(np.arange(W), np.arange(H))
-    for u, v in [(int(x), int(y)) for x, y in zip(us.ravel()[::37], vs.ravel()[::37])]:
+    seen = 0
+    for u, v in [(int(x), int(y)) for x, y in zip(us.ravel()[::7], vs.ravel()[::7])]:
         d = np.array([(u - CX) / F, (v - CY) / F, 1.0])
-        # the camera ray first: pixels that see the sphere are not wall pixels
+        # the camera ray first: pixels that see the sphere (nearer than the
+        # wall) show the sphere, not the wall
         oc = -c
         bq, cq = 2 * d @ oc, oc @ oc - r * r
         if bq * bq - 4 * (d @ d) * cq >= 0:
+            assert lf[v, u] == lf_ball[v, u] and lf_ball[v, u] > 0, (u, v)
+            seen += 1
             continue
         p = Z * d                                    # the wall point
         X = p - proj                                 # outside the projector's texture: unlit anyway
@@ -76,6 +85,40 @@ def test_projector_shadow_of_a_sphere():
             assert abs(lf[v, u] - gain * amb * albedo) < 1e-9, (u, v)
         else:
             assert lf[v, u] > gain * amb * albedo + 1.0, (u, v)
+    assert seen > 10
+
+
+def test_no_shadow_from_behind_the_projector():
+    # only what lies between a point and the projector blocks its light: a
+    # large panel behind the projector and the cameras changes nothing
+    pat = np.full((H, W), 255, dtype=np.uint8)
+    proj = (0.02, 0.0, 0.0)
+    scene = [_wall(1.0, albedo=0.6), oracle.sphere((0.05, 0.02, 0.5), 0.08, albedo=0.3)]
+    panel = oracle.rectangle((0.0, 0.0, -0.5), (3, 0, 0), (0, 3, 0), albedo=0.9)
+    _, _, a, _ = _render(scene, pat, proj=proj)
+    _, _, b, _ = _render(scene + [panel], pat, proj=proj)
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("metallic,roughness", [(0.0, 0.3), (0.5, 0.25), (1.0, 0.4)])
+def test_bsdf_is_reciprocal(metallic, roughness):
+    # Helmholtz reciprocity: f(i, o) = f(o, i).  Light a fronto-parallel wall
+    # at Z from the left camera's centre and look from the right camera, then
+    # swap the two roles.  A wall point p seen at right pixel u is seen at
+    # left pixel u + f b / Z; with ambient 0 and a uniform pattern its value
+    # is gain f E, E = power (n.i) / |p - light|^2 and n.i = Z / |p - light|,
+    # so value * |p - light|^3 must agree between the two renders.
+    pat = np.full((H, W), 255, dtype=np.uint8)
+    Z, disp = 0.8, 6
+    b = disp * Z / F
+    wall = _wall(Z, albedo=0.7, metallic=metallic, roughness=roughness)
+    _, _, _, rf = _render([wall], pat, baseline=b, proj=(0.0, 0.0, 0.0), ambient=0.0)
+    _, _, lf, _ = _render([wall], pat, baseline=b, proj=(b, 0.0, 0.0), ambient=0.0)
+    for v in range(8, H - 8, 5):
+        for u in range(8, W - disp - 8, 5):
+            p = np.array([(u - CX) * Z / F + b, (v - CY) * Z / F, Z])
+            da, db = np.linalg.norm(p), np.linalg.norm(p - np.array([b, 0.0, 0.0]))
+            np.testing.assert_allclose(rf[v, u] * da ** 3, lf[v, u + disp] * db ** 3, rtol=1e-9)
 
 
 def test_mix_is_linear_in_the_transmission_weight():

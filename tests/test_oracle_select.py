@@ -30,6 +30,12 @@ def test_uniqueness_ratio_threshold():
     # u = 0 disables the test
     _, mask, _, _ = oracle.select(S, 0, -1, False, 1.0)
     assert (mask[0] & 1).tolist() == [0, 0, 0]
+    # the boundary: (100 - u) S(d) = 100 S(d*) is unique (the test is >=)
+    #   d* = 1 (S = 17), far S(4) = 20: 85 * 20 = 1700 = 100 * 17 -> pass;
+    #   S(4) = 19: 1615 < 1700 -> fail
+    S = _vol([[200, 17, 30, 200, 20], [200, 17, 30, 200, 19]])
+    _, mask, _, _ = oracle.select(S, 15, -1, False, 1.0)
+    assert (mask[0] & 1).tolist() == [0, 1]
 
 
 def test_left_right_check_hand_worked():
@@ -50,6 +56,16 @@ def test_left_right_check_hand_worked():
     S2 = _vol([[9, 1], [5, 2], [3, 8], [6, 1]])
     _, m, _, _ = oracle.select(S2, 0, 5, False, 1.0)
     assert int(m[0, 0]) & 2 == 2
+
+
+def test_right_view_ties_take_the_smallest_disparity():
+    # W = 3, D = 2.  x=0 [4, 9] -> d*=0;  x=1 [9, 4] -> d*=1;  x=2 [5, 6] -> d*=0
+    # D_R(0): S(0, d=0) = 4 and S(1, d=1) = 4 tie -> the smaller d, 0
+    # with lr = 0: x=0 (xr=0) |0 - 0| = 0 passes, x=1 (xr=0) |1 - 0| = 1 fails
+    S = _vol([[4, 9], [9, 4], [5, 6]])
+    dstar, m, _, _ = oracle.select(S, 0, 0, False, 1.0)
+    assert dstar[0].tolist() == [0, 1, 0]
+    assert (m[0, :2] & 2).tolist() == [0, 2]
 
 
 def test_right_view_search_range_is_clipped_at_the_border():
