@@ -95,6 +95,9 @@
  *  - radiance L = f E + ambient * albedo, pixel = gain * L rounded half to
  *    even and clamped to [0, 255];
  *  - all in fp64 with + - * / and sqrt only, in a fixed order.
+ *  Parity unpinned for two constants: Schlick's exponent 5 and the
+ *  dielectric F0 = 0.04 are restated from the named approximations; no
+ *  independent fact fixes them (the rest of the renderer is pinned).
  *
  * Variants Sec. VI-D also names (optional in the stage):
  *  - centre-symmetric census (CSCT): for every offset o of the window that
