@@ -4,6 +4,7 @@ out-of-range parameters before any CUDA call is made."""
 import ctypes
 import os
 import re
+import subprocess
 
 import numpy as np
 import pytest
@@ -130,3 +131,47 @@ def test_batch_create_rejects_bad_arguments(lib):
     assert blib.simsense_batch_create(None, arr, 1) == -1
     assert blib.simsense_batch_destroy(None) == 0
     assert blib.simsense_batch_num_classes(None) == -1
+
+
+_C_CALLER = r"""
+#include "simsense.h"
+#include <stdio.h>
+#include <string.h>
+
+typedef void (*fn_t)(void);
+static const fn_t every_entry_point[] = {
+%(table)s
+};
+
+int main(void)
+{
+    simsense_t h = (simsense_t)0;
+    /* a window larger than the image: rejected before any CUDA call */
+    int rc = simsense_create(&h, 4, 4, 2, 7, 7, 86, 8, 15, 1, 920.0f, 0.055f);
+    if (rc != SIMSENSE_ERR_INVALID_ARG || h != (simsense_t)0) return 1;
+    if (simsense_destroy((simsense_t)0) != SIMSENSE_OK) return 2;
+    if (simsense_scratch_bytes((simsense_t)0) != 0) return 3;
+    if (strcmp(simsense_strerror(SIMSENSE_ERR_INVALID_ARG), "invalid argument") != 0) return 4;
+    printf("%%d entry points\n", (int)(sizeof every_entry_point / sizeof every_entry_point[0]));
+    return 0;
+}
+"""
+
+
+@pytest.mark.parametrize("compiler,std", [("gcc", "-std=c99"), ("g++", "-std=c++17")])
+def test_plain_c_and_cpp_callers_compile_link_and_run(lib, tmp_path, compiler, std):
+    # the boundary needs nothing but the header and the shared library: a C99
+    # (and a C++) caller that takes the address of every declared entry point
+    # compiles without warnings, links, and gets the documented status codes
+    # from the calls that fail before touching the GPU
+    from paper_2201_11924_gb300 import simsense
+    names = _declared_functions()
+    src = tmp_path / ("caller.c" if compiler == "gcc" else "caller.cpp")
+    src.write_text(_C_CALLER % {"table": ",\n".join(f"    (fn_t){n}" for n in names)})
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(simsense.LIB_PATH)
+    subprocess.run([compiler, std, "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-o", str(exe), f"-L{libdir}", "-lsimsense", f"-Wl,-rpath,{libdir}"], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
+    assert r.stdout.strip() == f"{len(names)} entry points"
