@@ -536,7 +536,7 @@ cudaError_t cost_code(const Params& p, const PairPtrs* pairs, int n, int* status
 //      2^16), so every input word is split into pairs once;
 //   2. for every output pixel and word, the sum of the bw staged columns and
 //      the division by the in-image pixel count n, a multiply-high by
-//      floor(2^32 / n) + 1, exact for every numerator below 2^16 and n <= 81.
+//      floor(2^32 / n) + 1, exact for every numerator below 2^16 and 2 <= n <= 81.
 // Lanes take consecutive words of one pixel: coalesced loads, conflict-free
 // shared-memory accesses.
 constexpr int kBlkPix = 32;
@@ -629,8 +629,10 @@ cudaError_t block_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStrea
 {
     PairTable<N> pt{};
     for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
+    // n = 1 (whose multiplier needs 33 bits) never reaches the kernel: such a
+    // block is the per-pixel cost, which runs without it (block_active)
     Magic mg{};
-    for (uint32_t k = 1; k < 82; k++) mg.m[k] = (uint32_t)(0x100000000ull / k) + 1u;
+    for (uint32_t k = 2; k < 82; k++) mg.m[k] = (uint32_t)(0x100000000ull / k) + 1u;
     const K<N> kernel = block_kernel_for<N>(p);
     dim3 grid((p.W + kBlkPix - 1) / kBlkPix, p.H, n);
     kernel<<<grid, 256, 0, s>>>(pt, p.W, p.H, mg);

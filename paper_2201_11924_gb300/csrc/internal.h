@@ -37,6 +37,16 @@ struct Params {
     int test_stall = 0;
 };
 
+// Whether the SGBM block cost changes anything: a block that covers a single
+// in-image pixel everywhere (1 pixel across in each direction where the
+// image is 1 pixel across or the block is) averages each cost with itself,
+// so the per-pixel cost is the block cost.  Otherwise every pixel's block
+// holds at least 2 in-image pixels.
+inline bool block_active(const Params& p)
+{
+    return (p.block_w > 1 && p.W > 1) || (p.block_h > 1 && p.H > 1);
+}
+
 // Applies a variant option to p (re-deriving nbits and the code width) after
 // checking the ranges; returns a SIMSENSE status.
 int set_variant(Params& p, int opt, int value);

@@ -99,7 +99,7 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
     }
     if (e != cudaSuccess) return cuda_fail(h, e);
     e = mark(h, SIMSENSE_STAGE_COST, false, st);
-    if (p.block_w > 1 || p.block_h > 1) {
+    if (block_active(p)) {
         // SGBM: the per-pixel costs go to the path volume (free until the
         // path stage), their block mean to the cost volume
         PairPtrs raw = pair;
