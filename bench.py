@@ -716,6 +716,11 @@ def main():
                 "stage_ms_per_step": {k: v / max(1, n_prof) for k, v in stage_ms.items()},
                 "hbm_algorithmic_bytes_per_frame": algorithmic_bytes(wl),
                 "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
+    if roofline["traffic"] is not None:
+        # the same launch against the HBM roof: its measured DRAM bytes over
+        # its live duration (how close its actual traffic runs to the copy peak)
+        roofline["traffic_gbs"] = roofline["traffic"] / launch_s / 1e9
+        roofline["traffic_frac_of_hbm_peak"] = roofline["traffic_gbs"] / roofline["hbm_peak_gbs"]
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
