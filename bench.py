@@ -209,6 +209,16 @@ def cpu_oracle_rate(wl, pair, budget_s=10.0, strip_rows=90):
     return cells / el, n, el
 
 
+def workload_config(wl):
+    """The keys both arms report for a workload."""
+    return {"workload": wl.name, "W": wl.W, "H": wl.H, "D": wl.D, "paths": wl.paths,
+            "census": f"{wl.win_w}x{wl.win_h}" + (" centre-symmetric" if wl.census_cs else ""),
+            "block": f"{wl.block[0]}x{wl.block[1]}", "median": wl.median,
+            "sensor_noise": "D415 (Sec. VI-C / VII)" if wl.noise else None,
+            "P1": wl.P1, "P2": wl.P2, "uniq": wl.uniq,
+            "lr_max_diff": wl.lr_max_diff, "subpixel": wl.subpixel}
+
+
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -242,8 +252,7 @@ def run_reference(args, wl):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": wl.name, "W": wl.W, "H": wl.H, "D": wl.D, "paths": wl.paths,
-                   "census": f"{wl.win_w}x{wl.win_h}"},
+        "config": {**workload_config(wl), "path": "CPU oracle, one thread, full-width strips"},
         "cells_per_s": cells / el,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -732,12 +741,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": el_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": wl.name, "W": wl.W, "H": wl.H, "D": wl.D, "paths": wl.paths,
-                   "census": f"{wl.win_w}x{wl.win_h}" + (" centre-symmetric" if wl.census_cs else ""),
-                   "block": f"{wl.block[0]}x{wl.block[1]}", "median": wl.median,
-                   "sensor_noise": "D415 (Sec. VI-C / VII)" if wl.noise else None,
-                   "P1": wl.P1, "P2": wl.P2, "uniq": wl.uniq,
-                   "lr_max_diff": wl.lr_max_diff, "subpixel": wl.subpixel, "pairs_cycled": n_pairs,
+        "config": {**workload_config(wl), "pairs_cycled": n_pairs,
                    "l2": "no flush: every step streams its own ~1 GB path volume through HBM, "
                          "far above the 129 MB L2", "path": "plain (one pair per call)"},
         "cells_per_s": value * wl.cells,
