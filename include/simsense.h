@@ -467,6 +467,20 @@ const char* simsense_strerror(int code);
 /* CUDA error code (cudaError_t) behind the handle's last SIMSENSE_ERR_CUDA. */
 int simsense_last_cuda_error(simsense_t h);
 
+/*
+ * Test hook for the out-of-memory paths: the nth device allocation the library
+ * makes from now on (1 = the next one) fails as if the device were out of
+ * memory, and the ones after it succeed again; 0 (or less) disarms it.  The
+ * allocations are those of simsense_create (the scratch buffers, in a fixed
+ * order: codes left and right, cost volume, path volume, status word, the
+ * two input and the depth staging buffers), simsense_set_rectify (map and
+ * image of the left view, then of the right) and simsense_batch_create
+ * (scratch, status word).  The failing call returns SIMSENSE_ERR_OOM and
+ * frees what it had allocated: a create leaves *out NULL, simsense_set_rectify
+ * leaves rectification off.  Process-wide; for tests, not for production use.
+ */
+void simsense_test_fail_allocation(int nth);
+
 #ifdef __cplusplus
 }
 #endif

@@ -115,6 +115,11 @@ struct Tuning {
 // its first call asks for the largest shared-memory carve-out.
 cudaError_t ensure_smem(const void* kernel, size_t bytes);
 
+// Every device allocation of the library's scratch (cudaMalloc, except that
+// the test hook simsense_test_fail_allocation can make one of them fail as
+// if the device were out of memory).
+cudaError_t dev_alloc(void** ptr, size_t bytes);
+
 // Optional outputs of the selection kernel (device pointers, may be null).
 struct SelectDebug {
     uint16_t* aggregated;

@@ -1,6 +1,7 @@
 // C ABI of libsimsense (declared in include/simsense.h): argument checks,
 // scratch ownership and the launch sequence census -> cost -> paths -> select.
 #include <math.h>
+#include <atomic>
 #include <new>
 
 #include "internal.h"
@@ -8,6 +9,25 @@
 #include <nvtx3/nvToolsExt.h>
 
 using namespace simsense;
+
+namespace {
+
+// allocations left before the one that fails (0: none fails)
+std::atomic<int> g_fail_alloc{0};
+
+}  // namespace
+
+cudaError_t simsense::dev_alloc(void** ptr, size_t bytes)
+{
+    int k = g_fail_alloc.load();
+    while (k > 0 && !g_fail_alloc.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
 
 namespace {
 
@@ -246,15 +266,15 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
     const size_t cost_bytes = npx * p.Dp;
     const size_t vol_bytes = (size_t)paths * npx * p.Dp;
     Scratch& s = h->s;
-    bool ok = cudaMalloc(&s.codes_left, code_bytes) == cudaSuccess &&
-              cudaMalloc(&s.codes_right, code_bytes) == cudaSuccess &&
-              cudaMalloc((void**)&s.cost, cost_bytes) == cudaSuccess &&
-              cudaMalloc((void**)&s.paths, vol_bytes) == cudaSuccess &&
-              cudaMalloc((void**)&s.status, sizeof(int)) == cudaSuccess &&
+    bool ok = dev_alloc(&s.codes_left, code_bytes) == cudaSuccess &&
+              dev_alloc(&s.codes_right, code_bytes) == cudaSuccess &&
+              dev_alloc((void**)&s.cost, cost_bytes) == cudaSuccess &&
+              dev_alloc((void**)&s.paths, vol_bytes) == cudaSuccess &&
+              dev_alloc((void**)&s.status, sizeof(int)) == cudaSuccess &&
               cudaMemset(s.status, 0, sizeof(int)) == cudaSuccess &&
-              cudaMalloc((void**)&s.stage_left, npx) == cudaSuccess &&
-              cudaMalloc((void**)&s.stage_right, npx) == cudaSuccess &&
-              cudaMalloc((void**)&s.stage_depth, npx * sizeof(float)) == cudaSuccess;
+              dev_alloc((void**)&s.stage_left, npx) == cudaSuccess &&
+              dev_alloc((void**)&s.stage_right, npx) == cudaSuccess &&
+              dev_alloc((void**)&s.stage_depth, npx * sizeof(float)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();   // clear the sticky-free allocation error
         free_scratch(s);
@@ -364,8 +384,8 @@ int simsense_set_rectify(simsense_t h, const simsense_camera_t* left, const sims
     if (!left) return SIMSENSE_OK;
     const size_t npx = (size_t)h->p.W * h->p.H;
     for (int v = 0; v < 2; v++) {
-        if (cudaMalloc((void**)&h->rect_map[v], npx * sizeof(short4)) != cudaSuccess ||
-            cudaMalloc((void**)&h->rect_img[v], npx) != cudaSuccess) {
+        if (dev_alloc((void**)&h->rect_map[v], npx * sizeof(short4)) != cudaSuccess ||
+            dev_alloc((void**)&h->rect_img[v], npx) != cudaSuccess) {
             cudaGetLastError();
             free_rectify(h);
             return SIMSENSE_ERR_OOM;
@@ -477,6 +497,11 @@ int simsense_destroy(simsense_t h)
     free_rectify(h);
     delete h;
     return SIMSENSE_OK;
+}
+
+void simsense_test_fail_allocation(int nth)
+{
+    g_fail_alloc.store(nth > 0 ? nth : 0);
 }
 
 const char* simsense_strerror(int code)

@@ -184,7 +184,7 @@ int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* p
         total += 2 * round256(npx * (p.wide_codes ? 8 : 4)) + round256(npx * p.Dp) +
                  round256(npx * p.paths * p.Dp);
     }
-    bool ok = cudaMalloc(&b->scratch, total) == cudaSuccess && cudaMalloc((void**)&b->status, sizeof(int)) == cudaSuccess &&
+    bool ok = dev_alloc(&b->scratch, total) == cudaSuccess && dev_alloc((void**)&b->status, sizeof(int)) == cudaSuccess &&
               cudaMemset(b->status, 0, sizeof(int)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
