@@ -131,8 +131,11 @@ class DepthServer:
         while an older one has no free slot, so the served mix is the
         arrival mix); "per_class" lets each class fill its own free slots
         (more concurrency, but under overload the classes' shares of the GPU
-        follow their slot counts, not the arrival mix)."""
+        follow their slot counts, not the arrival mix).
+        A request from a camera the server does not know is not served: it
+        is listed in ``self.rejected`` after the run."""
         waiting = {k: collections.deque() for k in self.classes}
+        rejected = []
         busy_cams = set()
         pending = collections.deque(trace)
         finished = []
@@ -163,6 +166,9 @@ class DepthServer:
             # 2. arrivals up to now join their class's queue
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
+                if not 0 <= r.camera < len(self.cameras):
+                    rejected.append(r)
+                    continue
                 w = self.cameras[r.camera]
                 waiting[(w.W, w.H, w.D)].append(r)
             # 3. admissions: classes by the arrival of their oldest waiting
@@ -203,6 +209,7 @@ class DepthServer:
             self.free[s.cls].append(s)
         self.busy = []
         self.backlog = sum(len(q) for q in waiting.values()) + len(pending)
+        self.rejected = rejected
         self.stats = {"iterations": iters, "mean_busy_slots": busy_sum / max(1, iters)}
         return finished
 
