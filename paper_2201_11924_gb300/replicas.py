@@ -47,22 +47,34 @@ class Replicas:
             dist.destroy_process_group()
 
 
-def from_env(backend: str | None = None) -> Replicas:
+# Seconds a collective (the barrier, the maximum) waits for the other ranks
+# before it fails: a rank that died or never joins ends the others' wait with
+# an error instead of the process group's default half hour.
+DEFAULT_TIMEOUT_S = 300.0
+
+
+def from_env(backend: str | None = None, timeout_s: float | None = None) -> Replicas:
     """Reads WORLD_SIZE / RANK / LOCAL_RANK (torchrun's variables) and, for
     more than one rank, joins the process group: NCCL when CUDA is available,
-    gloo otherwise (or the given backend)."""
+    gloo otherwise (or the given backend).  timeout_s (default: the
+    SIMSENSE_COLLECTIVE_TIMEOUT_S variable, else DEFAULT_TIMEOUT_S) bounds
+    every collective's wait for the other ranks."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world <= 1:
         return Replicas(1, 0, 0, None)
+    import datetime
+
     import torch
     import torch.distributed as dist
     if backend is None:
         backend = "nccl" if torch.cuda.is_available() else "gloo"
     if backend == "nccl":
         torch.cuda.set_device(local)
-    dist.init_process_group(backend)
+    if timeout_s is None:
+        timeout_s = float(os.environ.get("SIMSENSE_COLLECTIVE_TIMEOUT_S", DEFAULT_TIMEOUT_S))
+    dist.init_process_group(backend, timeout=datetime.timedelta(seconds=timeout_s))
     return Replicas(world, rank, local, backend)
 
 

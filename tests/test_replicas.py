@@ -63,3 +63,73 @@ def test_two_gloo_ranks_agree_on_the_slowest_time():
     assert all(r[2] == 11.0 for r in res)                       # max over ranks
     owned = sorted(u for r in res for u in r[3])
     assert owned == list(range(4 * world))                      # pairs split, none shared
+
+
+def _rank_that_leaves(rank, world, port, out):
+    # rank 1 joins the group and exits without reaching the barrier; rank 0
+    # must get an error from its barrier well before any default timeout
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE=str(world),
+                      RANK=str(rank), LOCAL_RANK=str(rank))
+    rep = replicas.from_env(backend="gloo", timeout_s=5.0)
+
+    def report_and_exit(*msg):
+        out.put(msg)
+        out.close()
+        out.join_thread()            # the message is written before the process ends
+        os._exit(0)                  # no interpreter shutdown around a broken group
+
+    if rank == 1:
+        report_and_exit(rank, "left", 0.0)
+    t0 = time.perf_counter()
+    try:
+        rep.barrier()
+        rep.max_over_ranks(1.0)
+        outcome = "no error"
+    except Exception as e:                       # gloo: timeout or connection closed
+        outcome = type(e).__name__
+    report_and_exit(rank, outcome, time.perf_counter() - t0)
+
+
+def test_a_rank_that_leaves_ends_the_others_wait_with_an_error():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    world, port = 2, _free_port()
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_that_leaves, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict((r, (o, t)) for r, o, t in (q.get(timeout=120) for _ in range(world)))
+    for p in procs:
+        p.join(timeout=60)
+    assert res[1][0] == "left"
+    outcome, waited = res[0]
+    assert outcome != "no error"
+    assert waited < 60.0
+
+
+def _lonely_rank(port, out):
+    import time
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), WORLD_SIZE="2", RANK="0", LOCAL_RANK="0")
+    t0 = time.perf_counter()
+    try:
+        replicas.from_env(backend="gloo", timeout_s=3.0)
+        outcome = "no error"
+    except Exception as e:                       # the rendezvous gives up
+        outcome = type(e).__name__
+    out.put((outcome, time.perf_counter() - t0))
+    out.close()
+    out.join_thread()
+    os._exit(0)
+
+
+def test_a_rank_that_never_joins_ends_the_rendezvous_with_an_error():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_lonely_rank, args=(_free_port(), q))
+    p.start()
+    outcome, waited = q.get(timeout=120)
+    p.join(timeout=60)
+    assert outcome != "no error"
+    assert waited < 60.0
