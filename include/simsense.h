@@ -36,7 +36,9 @@
  * Conventions for every call:
  *  - images are contiguous row-major with pitch W (no padding): uint8 H x W
  *    for the views, float32 H x W for depth; caller-owned; inputs and outputs
- *    must not overlap.
+ *    must not overlap.  Device buffers belong to the GPU that was current
+ *    when the handle was created (the calls switch to it); the library does
+ *    not check a pointer's GPU, the Python binding does.
  *  - the library owns its scratch memory: it is allocated by simsense_create
  *    and released by simsense_destroy; simsense_compute allocates nothing.
  *  - compute calls are asynchronous on the given CUDA stream (NULL = the

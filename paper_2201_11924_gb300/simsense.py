@@ -225,13 +225,20 @@ def _stream_ptr(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def _dev_ptr(t, dtype, shape, name):
+def _dev_ptr(t, dtype, shape, name, device=None):
+    """Device address of tensor t after checking its type, shape, layout and
+    GPU: device (an index) is the GPU the kernels run on, by default the
+    current one (a tensor on another GPU would be read through a foreign
+    address)."""
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}, "
                          f"got {t.dtype} {tuple(t.shape)}")
+    want = torch.cuda.current_device() if device is None else int(device)
+    if t.device.index != want:
+        raise ValueError(f"{name} is on cuda:{t.device.index}, but the kernels run on cuda:{want}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -249,6 +256,8 @@ class SimSense:
         if rc != OK:
             self._h = None
             raise SimsenseError(rc, "simsense_create")
+        import torch
+        self.device = torch.cuda.current_device()    # the GPU simsense_create bound the handle to
         if not subpixel:
             self.set_option(OPT_SUBPIXEL, 0)
 
@@ -321,9 +330,10 @@ class SimSense:
         shape = (self.H, self.W)
         if depth is None:
             depth = torch.empty(shape, dtype=torch.float32, device=left.device)
-        rc = load().simsense_compute(self.handle, _dev_ptr(left, torch.uint8, shape, "left"),
-                                     _dev_ptr(right, torch.uint8, shape, "right"),
-                                     _dev_ptr(depth, torch.float32, shape, "depth"), _stream_ptr(stream))
+        rc = load().simsense_compute(self.handle, _dev_ptr(left, torch.uint8, shape, "left", self.device),
+                                     _dev_ptr(right, torch.uint8, shape, "right", self.device),
+                                     _dev_ptr(depth, torch.float32, shape, "depth", self.device),
+                                     _stream_ptr(stream))
         self._check(rc, "simsense_compute")
         return depth
 
@@ -360,8 +370,8 @@ class SimSense:
                      out["aggregated"].data_ptr() if aggregated else None,
                      out["disparity_int"].data_ptr(), out["disparity"].data_ptr(), out["mask"].data_ptr())
         shape = (H, W)
-        rc = load().simsense_compute_debug(self.handle, _dev_ptr(left, torch.uint8, shape, "left"),
-                                           _dev_ptr(right, torch.uint8, shape, "right"),
+        rc = load().simsense_compute_debug(self.handle, _dev_ptr(left, torch.uint8, shape, "left", self.device),
+                                           _dev_ptr(right, torch.uint8, shape, "right", self.device),
                                            ctypes.c_void_p(out["depth"].data_ptr()), ctypes.byref(dbg),
                                            _stream_ptr(stream))
         self._check(rc, "simsense_compute_debug")
@@ -442,6 +452,8 @@ class SimSenseBatch:
         if rc != OK:
             self._h = None
             raise SimsenseError(rc, "simsense_batch_create")
+        import torch
+        self.device = torch.cuda.current_device()    # the GPU the batch was created on
 
     @property
     def handle(self):
@@ -464,9 +476,9 @@ class SimSenseBatch:
         Z = (ctypes.c_void_p * n)()
         for i, wl in enumerate(self.workloads):
             shape = (wl.H, wl.W)
-            L[i] = _dev_ptr(lefts[i], torch.uint8, shape, f"left[{i}]").value
-            R[i] = _dev_ptr(rights[i], torch.uint8, shape, f"right[{i}]").value
-            Z[i] = _dev_ptr(depths[i], torch.float32, shape, f"depth[{i}]").value
+            L[i] = _dev_ptr(lefts[i], torch.uint8, shape, f"left[{i}]", self.device).value
+            R[i] = _dev_ptr(rights[i], torch.uint8, shape, f"right[{i}]", self.device).value
+            Z[i] = _dev_ptr(depths[i], torch.float32, shape, f"depth[{i}]", self.device).value
         return L, R, Z
 
     def compute(self, lefts, rights, depths, stream=None):
