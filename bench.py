@@ -56,6 +56,44 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
 
 
+# Measured issue rates of this GPU (bench_oprates.cu, results per clock per
+# SM): a 32-bit integer add and a 32-bit minimum.
+MEASURED_ADD_PER_CLK_SM = 124
+MEASURED_MIN_PER_CLK_SM = 64
+
+
+def roofline_object(wl, stage_ms, n_prof, n_sm, peaks, peak_src):
+    """The bench line's roofline for the dominant kernel: its algorithmic
+    integer ops over its live duration (stage_ms summed over n_prof steps)
+    against the derived INT32 peak, with the measured add and minimum rates
+    and, where an ncu capture of the current source exists, its DRAM bytes
+    against the HBM peak."""
+    ops = algorithmic_ops(wl)
+    dom = max(stage_ms, key=stage_ms.get)
+    launch_s = stage_ms[dom] / 1e3 / max(1, n_prof)
+    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
+    int_peak = n_sm * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12        # T ops/s
+    achieved = ops[dom] / launch_s / 1e12
+    add_peak = n_sm * MEASURED_ADD_PER_CLK_SM * sm_max * 1e6 / 1e12
+    min_peak = n_sm * MEASURED_MIN_PER_CLK_SM * sm_max * 1e6 / 1e12
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": int_peak,
+                "unit": "Tops/s", "frac": achieved / int_peak, "traffic": measured_traffic(wl, dom),
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
+                "peak_source": f"derived: {n_sm} SMs x {INT32_LANES_PER_SM} INT32 lanes x {sm_max:.0f} MHz",
+                "peak_measured": {"add_tops": add_peak, "min_tops": min_peak,
+                                  "frac_of_add": achieved / add_peak,
+                                  "source": "bench_oprates.cu: 124 adds and 64 minima per clock per SM"},
+                "stage_ms_per_step": {k: v / max(1, n_prof) for k, v in stage_ms.items()},
+                "hbm_algorithmic_bytes_per_frame": algorithmic_bytes(wl),
+                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
+    if roofline["traffic"] is not None:
+        # the same launch against the HBM roof: its measured DRAM bytes over
+        # its live duration (how close its actual traffic runs to the copy peak)
+        roofline["traffic_gbs"] = roofline["traffic"] / launch_s / 1e9
+        roofline["traffic_frac_of_hbm_peak"] = roofline["traffic_gbs"] / roofline["hbm_peak_gbs"]
+    return roofline
+
+
 def algorithmic_ops(wl):
     """Scalar integer ops per launch of each kernel (no SIMD credit).
 
@@ -710,26 +748,9 @@ def main():
         return 0
 
     # roofline of the dominant kernel, from the live stage events
-    ops = algorithmic_ops(wl)
-    dom = max(stage_ms, key=stage_ms.get)
-    launch_s = stage_ms[dom] / 1e3 / max(1, n_prof)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks, peak_src = _peaks()
-    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
-    int_peak = n_sm * INT32_LANES_PER_SM * sm_max * 1e6 / 1e12        # T ops/s
-    achieved = ops[dom] / launch_s / 1e12
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": int_peak,
-                "unit": "Tops/s", "frac": achieved / int_peak, "traffic": measured_traffic(wl, dom),
-                "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "peak_source": f"derived: {n_sm} SMs x {INT32_LANES_PER_SM} INT32 lanes x {sm_max:.0f} MHz",
-                "stage_ms_per_step": {k: v / max(1, n_prof) for k, v in stage_ms.items()},
-                "hbm_algorithmic_bytes_per_frame": algorithmic_bytes(wl),
-                "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
-    if roofline["traffic"] is not None:
-        # the same launch against the HBM roof: its measured DRAM bytes over
-        # its live duration (how close its actual traffic runs to the copy peak)
-        roofline["traffic_gbs"] = roofline["traffic"] / launch_s / 1e9
-        roofline["traffic_frac_of_hbm_peak"] = roofline["traffic_gbs"] / roofline["hbm_peak_gbs"]
+    roofline = roofline_object(wl, stage_ms, n_prof, n_sm, peaks, peak_src)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
