@@ -123,6 +123,15 @@ MUTANTS = [
      "if (xx < 0 || xx >= W || yy < 0 || yy >= H) { n++; continue; }\n                        sum +="),
     ("median_one_above_the_middle", "variants", "out[y * W + x] = win[n / 2];", "out[y * W + x] = win[n / 2 + 1];"),
     ("median_border_reflected", "variants", "if (xx < 0) xx = 0;", "if (xx < 0) xx = -xx;"),
+    # the whole stage: how the variants are wired together
+    ("stage_csct_cost_with_full_census_width", "variants",
+     "int nbits = census_cs ? (ww * wh - 1) / 2 : ww * wh - 1;", "int nbits = ww * wh - 1;"),
+    ("stage_block_cost_only_when_both_sides_exceed_one", "variants",
+     "if (rc == ORACLE_OK && (bw > 1 || bh > 1)) {", "if (rc == ORACLE_OK && (bw > 1 && bh > 1)) {"),
+    ("stage_median_of_integer_disparities", "variants",
+     "d0[i] = msk[i] == 0 ? dsp[i] : 0.0;", "d0[i] = msk[i] == 0 ? (double)ds[i] : 0.0;"),
+    ("stage_median_keeps_unfiltered_depth", "variants",
+     "depth[i] = dsp[i] > 0.0 ? f * baseline / dsp[i] : 0.0;", "depth[i] = depth[i];"),
     # sensor noise
     ("philox_wrong_weyl_constant", "noise", "k0 += W0;", "k0 += W1;"),
     ("philox_seven_rounds", "noise", "round < 10; round++", "round < 7; round++"),

@@ -119,3 +119,49 @@ def test_variants_off_equal_the_plain_stage():
     b = oracle.compute(L, R, 16, 5, 5, 7, 60, 4, 10, 1, True, 300.0, 0.055, census_cs=False, block=(1, 1), median=0)
     for k in ("depth", "disp", "dstar", "mask"):
         assert np.array_equal(a[k], b[k])
+
+
+def _pair(seed, H=20, W=36, shift=3):
+    rng = np.random.default_rng(seed)
+    L = rng.integers(0, 256, (H, W), dtype=np.uint8)
+    R = np.roll(L, -shift, axis=1)
+    R[:, W - shift:] = rng.integers(0, 256, (H, shift), dtype=np.uint8)
+    return L, R
+
+
+@pytest.mark.parametrize("census_cs,block", [(True, (1, 1)), (False, (1, 5)), (False, (5, 1)),
+                                             (False, (3, 3)), (True, (3, 1))])
+def test_stage_composes_its_variant_steps(census_cs, block):
+    # with P1 = P2 = 0 every path reproduces the cost, so S = paths * C for the
+    # variant's own cost volume: the (centre-symmetric) census codes, their
+    # Hamming cost with nbits for x - d < 0 (nbits = (w h - 1) / 2 for the
+    # centre-symmetric census), then the block mean -- each step pinned on its own
+    L, R = _pair(21 + 3 * block[0] + block[1] + census_cs)
+    D, ww, wh, paths = 12, 5, 5, 4
+    codes = oracle.census_cs if census_cs else oracle.census
+    nbits = (ww * wh - 1) // 2 if census_cs else ww * wh - 1
+    C = oracle.cost(codes(L, ww, wh), codes(R, ww, wh), D, nbits)
+    assert (C[:, 0, 1:] == nbits).all()                     # x = 0, every d >= 1: x - d < 0
+    if block != (1, 1):
+        C = oracle.cost_block(C, *block)
+    o = oracle.compute(L, R, D, ww, wh, 0, 0, paths, 0, -1, False, 300.0, 0.055, want_S=True,
+                       census_cs=census_cs, block=block)
+    assert np.array_equal(o["S"], paths * C.astype(np.int32))
+
+
+def test_median_output_is_the_filtered_disparity_and_its_depth():
+    # the filter takes the disparity map after the checks (invalid pixels as 0)
+    # and the depth follows the filtered disparity: Z = f b / d, 0 where d <= 0
+    L, R = _pair(5, H=28, W=48, shift=4)
+    args = (L, R, 16, 5, 5, 7, 60, 4, 10, 1, True, 300.0, 0.055)
+    pre = oracle.compute(*args)
+    post = oracle.compute(*args, median=3)
+    d0 = np.where(pre["mask"] == 0, pre["disp"], 0.0)
+    want = scipy.ndimage.median_filter(d0, size=3, mode="nearest")
+    assert not np.array_equal(want, d0)                       # the filter changes this map
+    valid = want > 0
+    np.testing.assert_array_equal(post["disp"][valid], want[valid])
+    assert (post["disp"][~valid] == -1.0).all()
+    fb = float(np.float32(300.0)) * float(np.float32(0.055))
+    np.testing.assert_allclose(post["depth"][valid], fb / want[valid], rtol=1e-12)
+    assert (post["depth"][~valid] == 0.0).all()
