@@ -15,7 +15,11 @@ Every planted mistake changes some result the method defines (none is an
 equivalent rewrite), and every one stays inside its buffers, so a copy fails
 by a wrong value, never by a crash.  Left out on purpose: the constants of
 the named approximations the renderer restates (Schlick's exponent, the
-dielectric F0), which no independent fact fixes.
+dielectric F0), which no independent fact fixes, and two changes found to be
+equivalent rewrites: invalid pixels entering the median as -1 instead of 0
+(both sort below every valid disparity) and a rectification fraction of
+256/256 not carrying into the next tap (full weight on that tap gives the
+same value).
 """
 import os
 import subprocess
@@ -107,6 +111,9 @@ MUTANTS = [
     ("subpixel_factor_two_dropped", "select",
      "df = (double)ds + (sm - sp) / (2.0 * (sm + sp - 2.0 * s0));",
      "df = (double)ds + (sm - sp) / (sm + sp - 2.0 * s0);"),
+    ("subpixel_skips_d_one", "select", "ds >= 1 && ds <= D - 2", "ds >= 2 && ds <= D - 2"),
+    ("subpixel_skips_d_max_minus_one", "select", "ds >= 1 && ds <= D - 2", "ds >= 1 && ds <= D - 3"),
+    ("uniqueness_off_at_one_percent", "select", "if (uniq > 0) {", "if (uniq > 1) {"),
     ("zero_disparity_is_valid", "select", "            if (!(df > 0.0)) m |= 4;\n", ""),
     ("depth_from_integer_disparity", "select",
      "depth[y * W + x] = m == 0 ? fb / df : 0.0;", "depth[y * W + x] = m == 0 ? fb / (double)ds : 0.0;"),
@@ -153,6 +160,8 @@ MUTANTS = [
      "(uint32_t)ax * by * t[1] + bx * (uint32_t)ay * t[2]",
      "bx * (uint32_t)ay * t[1] + (uint32_t)ax * by * t[2]"),
     ("bilinear_truncated", "rectify", "+ 32768u) >> 16", ") >> 16"),
+    ("registration_splats_points_behind_the_camera", "rectify",
+     "            if (!(Z2 > 0.0)) continue;\n", "            if (Z2 == 0.0) continue;\n"),
     ("zbuffer_keeps_the_farthest", "rectify",
      "if (out[k] == 0.0f || z < out[k]) out[k] = z;", "if (out[k] == 0.0f || z > out[k]) out[k] = z;"),
     ("registration_splat_rounds_down", "rectify",

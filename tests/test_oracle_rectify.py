@@ -134,3 +134,12 @@ def test_registration_sideways_translation_shifts_the_image(tx, ty):
     want = np.zeros_like(depth)
     want[max(sy, 0):21 + min(sy, 0), max(sx, 0):31 + min(sx, 0)] = Z
     assert np.array_equal(out, want)
+
+
+def test_registration_camera_facing_away_sees_nothing():
+    # turned half a turn about the y axis, the RGB camera looks away from every
+    # point in front of the depth camera (Z' = -Z < 0): nothing is splatted
+    depth = np.full((12, 16), 1.2, dtype=np.float32)
+    R = [[-1, 0, 0], [0, 1, 0], [0, 0, -1]]
+    out = oracle.register(depth, 50.0, 50.0, 7.5, 5.5, 50.0, 50.0, 7.5, 5.5, np.array(R, float), [0, 0, 0], 16, 12)
+    assert not out.any()

@@ -36,6 +36,11 @@ def test_uniqueness_ratio_threshold():
     S = _vol([[200, 17, 30, 200, 20], [200, 17, 30, 200, 19]])
     _, mask, _, _ = oracle.select(S, 15, -1, False, 1.0)
     assert (mask[0] & 1).tolist() == [0, 1]
+    # u = 1, the smallest ratio that tests: a far candidate equal to S(d*)
+    # fails (99 * 100 < 100 * 100), one 2% above passes (99 * 102 >= 10000)
+    S = _vol([[300, 100, 300, 300, 100], [300, 100, 300, 300, 102]])
+    _, mask, _, _ = oracle.select(S, 1, -1, False, 1.0)
+    assert (mask[0] & 1).tolist() == [1, 0]
 
 
 def test_left_right_check_hand_worked():
@@ -93,6 +98,17 @@ def test_subpixel_recovers_parabola_vertex(k, frac):
     assert int(mask[0, 0]) == 0
     assert abs(disp[0, 0] - v) < 1e-12
     assert abs(depth[0, 0] - fb / v) < 1e-12 * fb / v
+
+
+@pytest.mark.parametrize("k,frac", [(1, 0.25), (1, -0.25), (1, 0.5), (1, 0.125), (14, 0.25), (14, -0.5),
+                                    (14, 0.5)])
+def test_subpixel_at_the_refinable_range_ends(k, frac):
+    # d* = 1 and d* = D - 2 are the first and last refined disparities
+    D, a, c = 16, 64, 10
+    v = k + frac
+    S = _vol([[int(a * (d - v) ** 2 + c) for d in range(D)]])
+    _, mask, disp, _ = oracle.select(S, 0, -1, True, 50.6)
+    assert int(mask[0, 0]) == 0 and abs(disp[0, 0] - v) < 1e-12
 
 
 def test_subpixel_off_and_at_range_ends():
