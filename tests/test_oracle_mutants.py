@@ -160,6 +160,12 @@ MUTANTS = [
      "(uint32_t)ax * by * t[1] + bx * (uint32_t)ay * t[2]",
      "bx * (uint32_t)ay * t[1] + (uint32_t)ax * by * t[2]"),
     ("bilinear_truncated", "rectify", "+ 32768u) >> 16", ") >> 16"),
+    ("raw_focal_lengths_swapped", "rectify",
+     "double ur = c->fx * xd + c->cx, vr = c->fy * yd + c->cy;",
+     "double ur = c->fy * xd + c->cx, vr = c->fx * yd + c->cy;"),
+    ("rgb_focal_lengths_swapped", "rectify",
+     "double u2 = fx2 * (X2 / Z2) + cx2, v2 = fy2 * (Y2 / Z2) + cy2;",
+     "double u2 = fy2 * (X2 / Z2) + cx2, v2 = fx2 * (Y2 / Z2) + cy2;"),
     ("registration_splats_points_behind_the_camera", "rectify",
      "            if (!(Z2 > 0.0)) continue;\n", "            if (Z2 == 0.0) continue;\n"),
     ("zbuffer_keeps_the_farthest", "rectify",
@@ -179,6 +185,9 @@ MUTANTS = [
      "double o[3] = {view ? rp->baseline : 0.0, 0.0, 0.0};", "double o[3] = {view ? -rp->baseline : 0.0, 0.0, 0.0};"),
     ("farthest_hit_wins", "render",
      "if (t > 0.0 && (best < 0 || t < tb))", "if (t > 0.0 && (best < 0 || t > tb))"),
+    ("rectangle_twice_as_wide", "render",
+     "if (s < -1.0 || s > 1.0 || w < -1.0 || w > 1.0) return -1.0;",
+     "if (s < -2.0 || s > 2.0 || w < -1.0 || w > 1.0) return -1.0;"),
     ("no_ambient_term", "render", "double L = rp->ambient * q->albedo;", "double L = 0.0;"),
 ]
 

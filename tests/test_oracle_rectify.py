@@ -18,9 +18,10 @@ def _img(H=40, W=48, seed=1):
     return np.random.default_rng(seed).integers(0, 256, (H, W), dtype=np.uint8)
 
 
-def test_identity_camera_returns_the_image():
+@pytest.mark.parametrize("fx,fy", [(300.0, 300.0), (250.0, 400.0)])
+def test_identity_camera_returns_the_image(fx, fy):
     img = _img()
-    cam = oracle.camera(300.0, 300.0, 23.5, 19.5)
+    cam = oracle.camera(fx, fy, 23.5, 19.5)
     assert np.array_equal(oracle.rectify(img, cam), img)
 
 
@@ -143,3 +144,14 @@ def test_registration_camera_facing_away_sees_nothing():
     R = [[-1, 0, 0], [0, 1, 0], [0, 0, -1]]
     out = oracle.register(depth, 50.0, 50.0, 7.5, 5.5, 50.0, 50.0, 7.5, 5.5, np.array(R, float), [0, 0, 0], 16, 12)
     assert not out.any()
+
+
+def test_registration_through_an_anisotropic_rgb_camera():
+    # one depth pixel (u, v) = (12, 3) at Z through the pinhole model:
+    # X = (u - cx) / f Z, Y = (v - cy) / f Z; the RGB camera (fx2 = 100,
+    # fy2 = 50, cx2 = 20, cy2 = 5.5) sees it at (100 * 4.5 / 50 + 20,
+    # 50 * (-2.5) / 50 + 5.5) = (29, 3)
+    depth = np.zeros((12, 16), dtype=np.float32)
+    depth[3, 12] = 1.75
+    out = oracle.register(depth, 50.0, 50.0, 7.5, 5.5, 100.0, 50.0, 20.0, 5.5, np.eye(3), [0, 0, 0], 40, 12)
+    assert list(zip(*np.nonzero(out))) == [(3, 29)] and out[3, 29] == np.float32(1.75)

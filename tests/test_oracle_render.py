@@ -146,3 +146,18 @@ def test_rays_that_miss_give_zero_and_rounding():
     l, r, lf, rf = _render([oracle.sphere((0, 0, 1.0), 0.1)], pat)
     assert l[0, 0] == 0 and lf[0, 0] == 0.0
     assert np.array_equal(l, np.clip(np.rint(lf), 0, 255).astype(np.uint8))
+
+
+def test_rectangle_silhouette_is_its_projected_extent():
+    # a fronto-parallel rectangle at Z = 1 with half-sizes 0.2 x 0.1 m, seen
+    # by the f = 60 px left camera, covers |u - cx| <= 12, |v - cy| <= 6;
+    # rays that miss give 0, hits at least the ambient term (pixels on the
+    # edge itself are left out: the edge is one rounding away either way)
+    pat = np.full((H, W), 255, dtype=np.uint8)
+    rect = oracle.rectangle((0.0, 0.0, 1.0), (0.2, 0, 0), (0, 0.1, 0), albedo=0.5)
+    _, _, lf, _ = _render([rect], pat, ambient=0.05)
+    us, vs = np.meshgrid(np.arange(W), np.arange(H))
+    du, dv = np.abs(us - CX), np.abs(vs - CY)
+    inside, outside = (du < 12) & (dv < 6), (du > 12) | (dv > 6)
+    assert (lf[inside] >= 400.0 * 0.05 * 0.5 - 1e-9).all()
+    assert (lf[outside] == 0.0).all()
