@@ -254,7 +254,7 @@ def workload_config(wl):
             "block": f"{wl.block[0]}x{wl.block[1]}", "median": wl.median,
             "sensor_noise": "D415 (Sec. VI-C / VII)" if wl.noise else None,
             "P1": wl.P1, "P2": wl.P2, "uniq": wl.uniq,
-            "lr_max_diff": wl.lr_max_diff, "subpixel": wl.subpixel}
+            "lr_max_diff": wl.lr_max_diff, "subpixel": wl.subpixel, "seed": wl.seed}
 
 
 def run_reference(args, wl):
@@ -773,6 +773,8 @@ def main():
         "roofline": roofline,
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "gpu": torch.cuda.get_device_name(dev),
+        "host_cores": os.cpu_count(),
     }
     print(json.dumps(line), flush=True)
     m.close()
