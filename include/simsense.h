@@ -124,7 +124,7 @@ typedef struct simsense_ctx* simsense_t;
 /*
  * Create a matcher for W x H pairs with disparities 0 .. D-1 (Sec. VI-D:
  * the stage's adjustable parameters).
- *   census_win   SIMSENSE_WIN(w, h) with odd w, h and w*h - 1 <= 64
+ *   census_win   SIMSENSE_WIN(w, h) with odd w, h <= 15 and 1 <= w*h - 1 <= 64
  *                (e.g. 5x5 -> 24 bits, 7x7 -> 48, 9x7 -> 62)
  *   P1, P2       SGM penalties, 0 <= P1 <= P2 and nbits + P2 <= 255
  *   paths        4 or 8

@@ -175,3 +175,49 @@ def test_plain_c_and_cpp_callers_compile_link_and_run(lib, tmp_path, compiler, s
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, (r.returncode, r.stdout, r.stderr)
     assert r.stdout.strip() == f"{len(names)} entry points"
+
+
+def _documented_valid(W, H, D, w, h, P1, P2, paths, uniq, f, b):
+    """The limits simsense.h states for simsense_create."""
+    hh = h or w
+    nbits = w * hh - 1
+    return (w % 2 == 1 and hh % 2 == 1 and 1 <= w <= 15 and 1 <= hh <= 15 and 1 <= nbits <= 64
+            and w <= W <= 8192 and hh <= H <= 16384 and 1 <= D <= 256 and D <= W
+            and 0 <= P1 <= P2 and nbits + P2 <= 255 and paths in (4, 8) and 0 <= uniq <= 99
+            and f > 0 and b > 0 and np.isfinite(f) and np.isfinite(b))
+
+
+def test_create_validation_matches_the_documented_limits(lib):
+    # one field of a valid argument set at a time, set to values on both
+    # sides of its documented limits: the invalid ones are refused with
+    # SIMSENSE_ERR_INVALID_ARG before any CUDA call, the valid ones get past
+    # validation (on this GPU-less host the device query then fails with
+    # SIMSENSE_ERR_CUDA)
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("on a GPU the valid sets would allocate their scratch")
+    base = dict(W=64, H=32, D=16, w=5, h=5, P1=7, P2=86, paths=4, uniq=15, f=920.0, b=0.055)
+    cand = {
+        "W": [0, 4, 5, 16, 8192, 8193], "H": [0, 4, 5, 16384, 16385],
+        "D": [-1, 0, 1, 63, 64, 65, 256, 257],
+        "w": [0, 1, 2, 3, 13, 15, 17], "h": [0, 1, 2, 3, 13, 15, 17],
+        "P1": [-1, 0, 86, 87], "P2": [-1, 6, 7, 230, 231, 255],
+        "paths": [0, 2, 4, 6, 8, 16], "uniq": [-1, 0, 1, 99, 100],
+        "f": [920.0, 1e-6, 0.0, -1.0, float("inf"), float("nan")],
+        "b": [0.055, 0.0, -0.1, float("inf"), float("nan")],
+    }
+    outcomes = {True: 0, False: 0}
+    for field, values in cand.items():
+        for v in values:
+            a = dict(base, **{field: v})
+            if field in ("w", "h"):                    # a big window needs a big enough image
+                a.update(W=8192, H=64, D=16)
+            valid = _documented_valid(a["W"], a["H"], a["D"], a["w"], a["h"], a["P1"], a["P2"], a["paths"],
+                                      a["uniq"], a["f"], a["b"])
+            hdl = ctypes.c_void_p()
+            rc = lib.simsense_create(ctypes.byref(hdl), a["W"], a["H"], a["D"], a["w"] | (a["h"] << 8), a["P1"],
+                                     a["P2"], a["paths"], a["uniq"], 1, a["f"], a["b"])
+            assert rc == (-3 if valid else -1), (field, v, rc)
+            assert not hdl.value
+            outcomes[valid] += 1
+    assert outcomes[True] >= 15 and outcomes[False] >= 30      # both sides of the limits
