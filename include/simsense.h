@@ -73,12 +73,11 @@ typedef struct simsense_ctx* simsense_t;
 #define SIMSENSE_OPT_SUBPIXEL       1     /* value 0/1, default 1 */
 #define SIMSENSE_OPT_PROFILE        2     /* value 0/1, default 0: time each stage */
 /*
- * Variants of the stage that Sec. VI-D names (arxiv 2201.11924: SimSense
- * "performs a center-symmetric census transform", "also supports semi-global
- * block matching (SGBM)" whose cost is "the hamming distance between the local
- * regions of the two pixels", and lists "median filtering" among the
- * disparity post-processing steps).  The paper defines none of them; the
- * library's readings:
+ * Variants of the stage that Sec. VI-D names (arxiv 2201.11924): a
+ * centre-symmetric census, semi-global block matching (SGBM), whose cost
+ * compares the regions around the two pixels by Hamming distance, and a
+ * median filter among the disparity post-processing steps.  The paper
+ * defines none of them; the library's readings:
  *  CENSUS_CS  value 0/1, default 0.  1: for every window offset o before the
  *             centre in raster order, bit = [I(p+o) < I(p-o)], a pair with a
  *             pixel outside the image gives 0; (w*h-1)/2 bits, first offset
@@ -252,10 +251,9 @@ int simsense_add_noise(const uint8_t* clean, uint8_t* noisy, int W, int H, float
 
 /*
  * Stereo rectification and depth registration (arxiv 2201.11924 Sec. VI-D:
- * the stage "first performs a stereo rectification to project the images onto
- * a common image plane" and ends with "an optional depth registration that
- * aligns the depth map to the RGB camera frame").  The paper gives no camera
- * model; the library's reading:
+ * the stage starts by rectifying the pair onto one image plane and can end by
+ * registering the depth map to the frame of the RGB camera).  The paper gives
+ * no camera model; the library's reading:
  *  - camera of one view: raw intrinsics (fx, fy, cx, cy) in pixels, Brown-
  *    Conrady distortion (k1, k2, k3 radial, p1, p2 tangential), rectifying
  *    rotation R (row-major; rectified ray = R * raw ray) and rectified
@@ -310,7 +308,7 @@ int simsense_register_depth(const float* depth, int W, int H, const simsense_reg
 
 /*
  * IR image formation of analytic scenes (arxiv 2201.11924 Sec. VI-A/VI-B: the
- * projector is "a textured spot light", surfaces use the BSDF mix
+ * projector is a spot light that throws a texture, surfaces use the BSDF mix
  * f = w_d f_d + (1 - w_d) f_s with w_d = (1 - metallic)(1 - transmission),
  * f_d Lambertian, f_s GGX, plus a weak ambient light).  The paper renders with
  * a Vulkan path tracer; the library's reading is a direct-light ray caster:

@@ -54,10 +54,10 @@
  *  rejection method (k >= 1), at most 16 attempts (if all are rejected,
  *  gamma = (k - 1/3) theta).
  *
- * Rectification and depth registration (Sec. VI-D: the stage "first
- *  performs a stereo rectification" and ends with "an optional depth
- *  registration that aligns the depth map to the RGB camera frame"; the paper
- *  gives no camera model).  Readings:
+ * Rectification and depth registration (Sec. VI-D: the stage starts by
+ *  rectifying the pair onto one image plane and can end by registering the
+ *  depth map to the frame of the RGB camera; the paper gives no camera
+ *  model).  Readings:
  *  - rectification: for rectified pixel (u, v), the ray R^T ((u - rcx)/rfx,
  *    (v - rcy)/rfy, 1) in the raw camera, normalised by its z, distorted by
  *    the Brown-Conrady model (k1, k2, k3 radial, p1, p2 tangential) and
@@ -165,8 +165,8 @@ static int hamming64(uint64_t a, uint64_t b)
     return n;
 }
 
-/* Hamming matching cost volume (Sec. VI-D: "hamming distance as the cost
- * function").  C: H x W x D bytes, index (y*W + x)*D + d. */
+/* Hamming matching cost volume (Sec. VI-D: the matching cost is the Hamming
+ * distance of the census codes).  C: H x W x D bytes, index (y*W + x)*D + d. */
 int oracle_cost(const uint64_t* cL, const uint64_t* cR, int W, int H, int D, int nbits, uint8_t* C)
 {
     if (!cL || !cR || !C || W <= 0 || H <= 0 || D <= 0 || nbits < 0 || nbits > 64) return ORACLE_BAD_ARG;

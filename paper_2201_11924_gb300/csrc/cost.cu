@@ -1,6 +1,6 @@
-// Hamming matching cost volume (arxiv 2201.11924 Sec. VI-D: "hamming distance
-// as the cost function"; the section computes the cost from shared memory for
-// data reuse).
+// Hamming matching cost volume (arxiv 2201.11924 Sec. VI-D: the matching cost
+// is the Hamming distance of the census codes; the section computes it from
+// shared memory for data reuse).
 //
 // C(x, y, d) = popcount(cL(x, y) ^ cR(x - d, y)) for x - d >= 0, else nbits,
 // stored once per cell as a byte, layout [y][x][Dp] (d fastest).  Every SGM

@@ -1,7 +1,6 @@
 // Stereo rectification and depth registration (arxiv 2201.11924 Sec. VI-D:
-// SimSense "first performs a stereo rectification to project the images onto
-// a common image plane" and ends with "an optional depth registration that
-// aligns the depth map to the RGB camera frame").
+// the stage starts by rectifying the pair onto one image plane and can end by
+// registering the depth map to the frame of the RGB camera).
 //
 // Camera model (the paper gives none): pinhole with Brown-Conrady distortion
 // and a rectifying rotation.  For rectified pixel (u, v) the raw position is

@@ -1,6 +1,6 @@
 // SGM cost aggregation along scanline paths (arxiv 2201.11924 Sec. VI-D:
-// semi-global matching with Hamming cost; cost aggregation "accelerated with
-// warp-based optimization").
+// semi-global matching on the Hamming cost, with the aggregation organised
+// around warps).
 //
 // Every path direction r splits the image into independent scanlines (rows,
 // columns or diagonals).  A group of G lanes walks one scanline (a warp walks
