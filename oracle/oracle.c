@@ -347,8 +347,8 @@ int oracle_census_cs(const uint8_t* img, int W, int H, int ww, int wh, uint64_t*
     return ORACLE_OK;
 }
 
-/* SGBM block cost (Sec. VI-D: SGBM compares the local regions of the two
- * pixels): the mean of C over the bw x bh block centred on each pixel, over
+/* SGBM block cost (Sec. VI-D: the SGBM variant matches neighbourhoods, not
+ * single pixels): the mean of C over the bw x bh block centred on each pixel, over
  * the block's pixels inside the image, rounded half up.
  * C, Cb: H x W x D bytes (Cb must not alias C). */
 int oracle_cost_block(const uint8_t* C, int W, int H, int D, int bw, int bh, uint8_t* Cb)

@@ -525,8 +525,8 @@ cudaError_t cost_code(const Params& p, const PairPtrs* pairs, int n, int* status
     return p.wide_codes ? cost_dp<2, N>(p, pt, n, status, s) : cost_dp<1, N>(p, pt, n, status, s);
 }
 
-// SGBM block cost (the variant Sec. VI-D describes: the Hamming distance
-// between the local regions of the two pixels): the per-pixel cost volume
+// SGBM block cost (the variant Sec. VI-D describes, which matches
+// neighbourhoods rather than single pixels): the per-pixel cost volume
 // `raw` averaged over the bw x bh block around each pixel (same d), over the
 // block's pixels inside the image, rounded half up, into `out`.
 // A block takes 32 pixels of one output row in two separable passes:
