@@ -221,3 +221,17 @@ def test_create_validation_matches_the_documented_limits(lib):
             assert not hdl.value
             outcomes[valid] += 1
     assert outcomes[True] >= 15 and outcomes[False] >= 30      # both sides of the limits
+
+
+def test_binding_constants_match_the_header(lib):
+    # the Python binding repeats the header's status and option codes
+    from paper_2201_11924_gb300 import simsense
+    text = open(os.path.join(ROOT, "include", "simsense.h")).read()
+    defs = dict(re.findall(r"^#define SIMSENSE_((?:OK|ERR_\w+|OPT_\w+))\s+(-?\d+)", text, flags=re.M))
+    assert set(defs) >= {"OK", "ERR_INVALID_ARG", "ERR_OOM", "ERR_CUDA", "ERR_TIMEOUT", "OPT_SUBPIXEL"}
+    for name, value in defs.items():
+        assert getattr(simsense, name) == int(value), name
+    # every status has its own description, and an unknown one is named as such
+    texts = {code: simsense.strerror(int(v)) for code, v in defs.items() if code == "OK" or code.startswith("ERR_")}
+    assert len(set(texts.values())) == len(texts)
+    assert simsense.strerror(-99) == "unknown status"
