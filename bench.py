@@ -56,7 +56,7 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
 
 
-# Measured issue rates of this GPU (bench_oprates.cu, results per clock per
+# Measured issue rates of this GPU (probes/op_rates.cu, results per clock per
 # SM): a 32-bit integer add and a 32-bit minimum.
 MEASURED_ADD_PER_CLK_SM = 124
 MEASURED_MIN_PER_CLK_SM = 64
@@ -82,7 +82,7 @@ def roofline_object(wl, stage_ms, n_prof, n_sm, peaks, peak_src):
                 "peak_source": f"derived: {n_sm} SMs x {INT32_LANES_PER_SM} INT32 lanes x {sm_max:.0f} MHz",
                 "peak_measured": {"add_tops": add_peak, "min_tops": min_peak,
                                   "frac_of_add": achieved / add_peak,
-                                  "source": "bench_oprates.cu: 124 adds and 64 minima per clock per SM"},
+                                  "source": "probes/op_rates.cu: 124 adds and 64 minima per clock per SM"},
                 "stage_ms_per_step": {k: v / max(1, n_prof) for k, v in stage_ms.items()},
                 "hbm_algorithmic_bytes_per_frame": algorithmic_bytes(wl),
                 "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
@@ -124,8 +124,8 @@ def algorithmic_ops(wl):
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one
-# ncu capture (profiles/ncu_paths_dram_1280x720_D128_8path.md), with the SHA-1
-# of the kernel's source at the time: a changed source reports null.
+# one-kernel ncu capture of the dram__bytes counters, with the SHA-1 of the
+# kernel's source at the time: a changed source reports null.
 MEASURED_TRAFFIC = {
     "1280x720_D128_census7x7_8path": {
         # (the captured source differed from this one in its opening comment

@@ -204,21 +204,39 @@ int simsense_compute_debug(simsense_t h, const uint8_t* left_u8, const uint8_t* 
  *     with code bytes = 4 when w*h - 1 <= 32 else 8, and Dp = 64 * ceil(D/64).  Larger problems, like
  *     any other out-of-range argument, return SIMSENSE_ERR_INVALID_ARG.
  *     (320x240, D = 64, 4 paths fits; 1280x720 does not.)
- *   - The first call on a device looks up the array's device address with that
- *     device current (a one-time set-up per device); make that first call
- *     before any stream capture.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current (a one-time set-up per device).  With lazy module
+ *     loading (the CUDA default) that lookup also loads the library's device
+ *     code on the device, which is when the array is reserved: a caller whose
+ *     memory pool takes the rest of the device should make this first call at
+ *     start-up, before the pool grows and before any stream capture.  The
+ *     cached address is not refreshed after cudaDeviceReset.
  *   - All calls share the one array: calls whose kernels overlap on the GPU
  *     (different streams or threads) race; order them, e.g. on one stream.
  *     Nothing in the array needs clearing between calls, since every byte a
  *     call reads is written earlier in the same call.
+ *   - Bounded device-side waits that give up record SIMSENSE_ERR_TIMEOUT in a
+ *     status word of the same kind (one per GPU, in the library image, zero
+ *     at load); simsense_noalloc_status reads it.
  * Asynchronous on stream like simsense_compute; SIMSENSE_ERR_CUDA reports a
- * failed launch (there is no handle to keep the CUDA error code).
+ * failed launch (there is no handle to keep the CUDA error code; the error is
+ * cleared so that it does not reach the caller's next CUDA call).
  */
 #define SIMSENSE_NOALLOC_SCRATCH_BYTES (32u << 20)
 int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* right_u8, float* depth_f32,
                              int W, int H, int D, int census_win, int P1, int P2, int paths,
                              int uniq_ratio, int lr_max_diff, float f, float baseline,
                              int subpixel, struct CUstream_st* stream);
+
+/*
+ * Device-side status of the no-allocation calls on the current GPU (the
+ * paper has no counterpart): like simsense_device_status, synchronises
+ * `stream`, returns SIMSENSE_OK or the status recorded since the last read
+ * (SIMSENSE_ERR_TIMEOUT if a bounded wait of a call gave up; that call's depth
+ * is then undefined) and clears it.  Allocates nothing (the word lives next to
+ * the scratch array); SIMSENSE_ERR_CUDA if the copy fails.
+ */
+int simsense_noalloc_status(struct CUstream_st* stream);
 
 /*
  * IR sensor noise (arxiv 2201.11924 Sec. VI-C): I_noisy = gamma * I_clean + n

@@ -143,6 +143,13 @@ cudaError_t launch_paths(const Params& p, const PairPtrs* pairs, int n, const Tu
 cudaError_t launch_select(const Params& p, const PairPtrs* pairs, int n, const Tuning& t,
                           const SelectDebug& dbg, int* status, cudaStream_t s);
 
+// Bytes of the path volume of one pair (what the path kernel writes and the
+// selection kernel reads).
+inline size_t path_volume_bytes(const Params& p)
+{
+    return (size_t)p.paths * p.W * p.H * p.Dp;
+}
+
 // Validation and derived fields shared by every entry point that takes a
 // parameter set (the ranges of simsense_create).
 int make_params(Params& p, int W, int H, int D, int census_win, int P1, int P2, int paths,

@@ -21,6 +21,13 @@
 //  - nothing in the array has to start at zero: every byte a call reads was
 //    written earlier in that same call, so leftovers of a previous call are
 //    harmless;
+//  - the status word is sticky: a call whose bounded wait gave up leaves
+//    SIMSENSE_ERR_TIMEOUT there until simsense_noalloc_status reads and clears
+//    it (it starts at zero when the module loads);
+//  - the first call on a device looks up the array's address (and, with lazy
+//    module loading, loads the library's device code there, which is when the
+//    array is reserved), so it belongs in the caller's start-up, before any
+//    stream capture;
 //  - problems whose scratch does not fit are rejected.
 #include <mutex>
 
@@ -28,32 +35,52 @@
 
 using namespace simsense;
 
-// The scratch itself.  In host code this name is only a stand-in for the
-// device symbol, never a device address: it must be translated with
-// cudaGetSymbolAddress before a kernel may be given it.
+// The scratch itself, and the status word of the calls' bounded device-side
+// waits (SIMSENSE_ERR_TIMEOUT once one gave up; zero when the module loads).
+// In host code these names are only stand-ins for the device symbols, never
+// device addresses: they must be translated with cudaGetSymbolAddress before a
+// kernel may be given them.
 static __device__ __align__(256) uint8_t g_noalloc_scratch[SIMSENSE_NOALLOC_SCRATCH_BYTES];
+static __device__ int g_noalloc_status;
 
 namespace {
 
 constexpr int kMaxDevices = 128;
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices];   // device address of g_noalloc_scratch, per device
+struct Addrs {
+    void* scratch = nullptr;   // device address of g_noalloc_scratch
+    int* status = nullptr;     // device address of g_noalloc_status
+};
+Addrs g_addr[kMaxDevices];     // per device
 
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
-int scratch_address(void** out)
+// Device addresses of the scratch array and the status word on the current
+// device, looked up once per device (with that device current) and cached.
+// Under lazy module loading the first lookup also loads the library's device
+// code on that device and reserves the array there.  The cache is not
+// refreshed after cudaDeviceReset.
+int device_addrs(Addrs* out)
 {
     int dev = -1;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SIMSENSE_ERR_CUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return SIMSENSE_ERR_CUDA;
+    }
     if (dev < 0 || dev >= kMaxDevices) return SIMSENSE_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
+    Addrs& a = g_addr[dev];
+    if (!a.scratch || !a.status) {
         void* p = nullptr;
+        void* q = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return SIMSENSE_ERR_CUDA;
-        g_scratch_addr[dev] = p;
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&q, g_noalloc_status);
+        if (e != cudaSuccess || !p || !q) {
+            cudaGetLastError();   // leave no error pending for the caller's next CUDA call
+            return SIMSENSE_ERR_CUDA;
+        }
+        a.scratch = p;
+        a.status = static_cast<int*>(q);
     }
-    *out = g_scratch_addr[dev];
+    *out = a;
     return SIMSENSE_OK;
 }
 
@@ -76,13 +103,13 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
     const size_t npx = (size_t)W * H;
     const size_t code_bytes = round256(npx * (p.wide_codes ? 8 : 4));
     const size_t cost_bytes = round256(npx * p.Dp);
-    const size_t vol_bytes = (size_t)paths * npx * p.Dp;
+    const size_t vol_bytes = path_volume_bytes(p);
     if (2 * code_bytes + cost_bytes + vol_bytes > (size_t)SIMSENSE_NOALLOC_SCRATCH_BYTES)
         return SIMSENSE_ERR_INVALID_ARG;
-    void* base = nullptr;
-    rc = scratch_address(&base);
+    Addrs a;
+    rc = device_addrs(&a);
     if (rc != SIMSENSE_OK) return rc;
-    uint8_t* b = static_cast<uint8_t*>(base);
+    uint8_t* b = static_cast<uint8_t*>(a.scratch);
     void* codes_left = b;
     void* codes_right = b + code_bytes;
     uint8_t* cost = b + 2 * code_bytes;
@@ -93,8 +120,30 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
     const Tuning tune{};
     const SelectDebug none{};
     cudaError_t e = launch_census(p, &pair, 1, st);
-    if (e == cudaSuccess) e = launch_cost(p, &pair, 1, nullptr, st);
+    if (e == cudaSuccess) e = launch_cost(p, &pair, 1, a.status, st);
     if (e == cudaSuccess) e = launch_paths(p, &pair, 1, tune, st);
-    if (e == cudaSuccess) e = launch_select(p, &pair, 1, tune, none, nullptr, st);
-    return e == cudaSuccess ? SIMSENSE_OK : SIMSENSE_ERR_CUDA;
+    if (e == cudaSuccess) e = launch_select(p, &pair, 1, tune, none, a.status, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SIMSENSE_ERR_CUDA;
+    }
+    return SIMSENSE_OK;
+}
+
+extern "C" int simsense_noalloc_status(struct CUstream_st* stream)
+{
+    Addrs a;
+    const int rc = device_addrs(&a);
+    if (rc != SIMSENSE_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, a.status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && v != 0) e = cudaMemsetAsync(a.status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return SIMSENSE_ERR_CUDA;
+    }
+    return v == 0 ? SIMSENSE_OK : v;
 }

@@ -1,5 +1,7 @@
-// Per-SM issue rates of the instructions an SGM recurrence can use (GB300 probe).
-// Build and run: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/oprates bench_oprates.cu && /tmp/oprates
+// Per-SM issue rates of the instructions an SGM recurrence can use, measured on
+// the GPU: the measured peaks the benchmark line quotes beside the derived
+// INT32 peak come from this probe (it is not part of the library).
+// Build and run: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o /tmp/oprates paper_2201_11924_gb300/probes/op_rates.cu && /tmp/oprates
 // grid = #SMs blocks x 1024 threads, each thread 8 dependent-rotating chains.
 #include <cstdio>
 #include <cstdint>
