@@ -168,6 +168,13 @@ int simsense_compute_host(simsense_t h, const uint8_t* left_host, const uint8_t*
  *   disparity          H x W float32, d_f of a valid pixel, -1.0f otherwise
  *   mask               H x W uint8, bit 1 = uniqueness failed,
  *                      bit 2 = left-right check failed, bit 4 = d_f <= 0
+ *   cost               H x W x D uint8, the matching cost C(x, y, d) at
+ *                      (y*W + x)*D + d (the block cost with SIMSENSE_OPT_BLOCK)
+ *   paths              paths x H x W x D uint8, L_r(x, y, d) of direction r
+ *                      at ((r*H + y)*W + x)*D + d, r in the order ->, <-,
+ *                      down, up, down-right, down-left, up-right, up-left
+ *                      (each path cost is at most nbits + P2 <= 255), copied
+ *                      from the path volume the path kernel wrote
  */
 typedef struct simsense_debug {
     uint64_t* census_left;
@@ -176,6 +183,8 @@ typedef struct simsense_debug {
     int16_t* disparity_int;
     float* disparity;
     uint8_t* mask;
+    uint8_t* cost;
+    uint8_t* paths;
 } simsense_debug_t;
 
 /* simsense_compute plus the intermediate results named in *dbg (device

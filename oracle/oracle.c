@@ -95,9 +95,11 @@
  *  - radiance L = f E + ambient * albedo, pixel = gain * L rounded half to
  *    even and clamped to [0, 255];
  *  - all in fp64 with + - * / and sqrt only, in a fixed order.
- *  Parity unpinned for two constants: Schlick's exponent 5 and the
- *  dielectric F0 = 0.04 are restated from the named approximations; no
- *  independent fact fixes them (the rest of the renderer is pinned).
+ *  The two constants of the named approximations are pinned against the
+ *  exact Fresnel equations for a dielectric of refractive index 1.5: F0 =
+ *  0.04 is the reflectance at normal incidence ((n-1)/(n+1))^2, and with the
+ *  exponent 5 Schlick's form stays within 0.04 of the exact reflectance from
+ *  grazing to normal incidence (the exponents 4 and 6 do not).
  *
  * Variants Sec. VI-D also names (optional in the stage):
  *  - centre-symmetric census (CSCT): for every offset o of the window that

@@ -139,7 +139,14 @@ cudaError_t launch_block_cost(const Params& p, const PairPtrs* pairs, int n, cud
 // k x k median filter of the disparity map disp (invalid = 0) into depth,
 // and the filtered disparity (invalid = -1) into disp_out when it is not null.
 cudaError_t launch_median(const Params& p, const float* disp, float* depth, float* disp_out, cudaStream_t s);
-cudaError_t launch_paths(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s);
+// Path aggregation: the path volume holds, per pixel, P planes of L_r bytes.
+// dbg_paths (n == 1 only; may be null): paths x H x W x D bytes of every L_r,
+// direction r in the oracle's order (->, <-, down, up, down-right, down-left,
+// up-right, up-left), copied from the path kernel's output.
+cudaError_t launch_paths(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, uint8_t* dbg_paths,
+                         cudaStream_t s);
+// The L_r planes of vol into the dense debug layout.
+cudaError_t launch_unpack_paths(const Params& p, const uint8_t* vol, uint8_t* dbg_paths, cudaStream_t s);
 cudaError_t launch_select(const Params& p, const PairPtrs* pairs, int n, const Tuning& t,
                           const SelectDebug& dbg, int* status, cudaStream_t s);
 

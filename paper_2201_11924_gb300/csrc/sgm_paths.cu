@@ -431,13 +431,27 @@ cudaError_t paths_dp(const Params& p, const PairPtrs* pairs, int n, const Tuning
 
 }  // namespace
 
-cudaError_t launch_paths(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, cudaStream_t s)
+cudaError_t launch_unpack_paths(const Params& p, const uint8_t* vol, uint8_t* dbg_paths, cudaStream_t s)
+{
+    // plane r of every pixel ([y][x][r][Dp]) to [r][y][x][D]
+    const size_t npx = (size_t)p.W * p.H;
+    for (int r = 0; r < p.paths; r++) {
+        cudaError_t e = cudaMemcpy2DAsync(dbg_paths + r * npx * p.D, p.D, vol + (size_t)r * p.Dp,
+                                          (size_t)p.paths * p.Dp, p.D, npx, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_paths(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, uint8_t* dbg_paths,
+                         cudaStream_t s)
 {
     for (int b = 0; b < n; b += kMaxBatch) {
         const int c = n - b < kMaxBatch ? n - b : kMaxBatch;
         cudaError_t e = c == 1 ? paths_dp<1>(p, pairs + b, 1, t, s) : paths_dp<kMaxBatch>(p, pairs + b, c, t, s);
         if (e != cudaSuccess) return e;
     }
+    if (dbg_paths && n == 1) return launch_unpack_paths(p, pairs[0].vol, dbg_paths, s);
     return cudaSuccess;
 }
 

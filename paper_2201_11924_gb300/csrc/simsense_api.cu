@@ -134,8 +134,22 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
         if (e == cudaSuccess) e = e_end;
     }
     if (e != cudaSuccess) return cuda_fail(h, e);
+    // debug dumps of the census codes and of the cost volume, read before the
+    // path stage (the median variant reuses the left codes' memory later)
+    if (dbg && dbg->census_left) {
+        e = launch_widen_codes(p, s.codes_left, dbg->census_left, st);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+    }
+    if (dbg && dbg->census_right) {
+        e = launch_widen_codes(p, s.codes_right, dbg->census_right, st);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+    }
+    if (dbg && dbg->cost) {
+        e = cudaMemcpy2DAsync(dbg->cost, p.D, s.cost, p.Dp, p.D, (size_t)p.W * p.H, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e);
+    }
     e = mark(h, SIMSENSE_STAGE_PATHS, false, st);
-    if (e == cudaSuccess) e = launch_paths(p, &pair, 1, tune, st);
+    if (e == cudaSuccess) e = launch_paths(p, &pair, 1, tune, dbg ? dbg->paths : nullptr, st);
     {
         const cudaError_t e_end = mark(h, SIMSENSE_STAGE_PATHS, true, st);   // pops the range in any case
         if (e == cudaSuccess) e = e_end;
@@ -150,10 +164,11 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
     }
     e = mark(h, SIMSENSE_STAGE_SELECT, false, st);
     if (p.median > 1) {
-        // the selection writes the disparity into the cost volume (free after
-        // the path stage), the median filter turns it into depth
+        // the selection writes the disparity into the left census codes' memory
+        // (at least 4 bytes per pixel, free after the cost stage), the median
+        // filter turns it into depth
         PairPtrs sel = pair;
-        sel.depth = reinterpret_cast<float*>(s.cost);
+        sel.depth = reinterpret_cast<float*>(s.codes_left);
         if (e == cudaSuccess) e = launch_select(p, &sel, 1, tune, sd, s.status, st);
         if (e == cudaSuccess) e = launch_median(p, sel.depth, depth, sd.disparity, st);
     } else if (e == cudaSuccess) {
@@ -165,14 +180,6 @@ int run(simsense_ctx* h, const uint8_t* left, const uint8_t* right, float* depth
     }
     if (e != cudaSuccess) return cuda_fail(h, e);
     if (h->prof.on && h->prof.count < ProfileRing::kSlots) h->prof.count++;
-    if (dbg && dbg->census_left) {
-        e = launch_widen_codes(p, s.codes_left, dbg->census_left, st);
-        if (e != cudaSuccess) return cuda_fail(h, e);
-    }
-    if (dbg && dbg->census_right) {
-        e = launch_widen_codes(p, s.codes_right, dbg->census_right, st);
-        if (e != cudaSuccess) return cuda_fail(h, e);
-    }
     return SIMSENSE_OK;
 }
 
@@ -264,7 +271,7 @@ int simsense_create(simsense_t* out, int W, int H, int D, int census_win, int P1
     const size_t npx = (size_t)W * H;
     const size_t code_bytes = npx * (p.wide_codes ? 8 : 4);
     const size_t cost_bytes = npx * p.Dp;
-    const size_t vol_bytes = (size_t)paths * npx * p.Dp;
+    const size_t vol_bytes = path_volume_bytes(p);
     Scratch& s = h->s;
     bool ok = dev_alloc(&s.codes_left, code_bytes) == cudaSuccess &&
               dev_alloc(&s.codes_right, code_bytes) == cudaSuccess &&

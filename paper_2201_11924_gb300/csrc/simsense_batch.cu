@@ -107,7 +107,7 @@ cudaError_t enqueue_class(simsense_batch* b, const BatchClass& c, cudaStream_t s
     const SelectDebug none{};
     cudaError_t e = launch_census(c.p, pp.data(), n, s);
     if (e == cudaSuccess) e = launch_cost(c.p, pp.data(), n, b->status, s);
-    if (e == cudaSuccess) e = launch_paths(c.p, pp.data(), n, c.tune, s);
+    if (e == cudaSuccess) e = launch_paths(c.p, pp.data(), n, c.tune, nullptr, s);
     if (e == cudaSuccess) e = launch_select(c.p, pp.data(), n, c.tune, none, b->status, s);
     return e;
 }
@@ -182,7 +182,7 @@ int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* p
         const size_t npx = (size_t)p.W * p.H;
         off[i] = total;
         total += 2 * round256(npx * (p.wide_codes ? 8 : 4)) + round256(npx * p.Dp) +
-                 round256(npx * p.paths * p.Dp);
+                 round256(path_volume_bytes(p));
     }
     bool ok = dev_alloc(&b->scratch, total) == cudaSuccess && dev_alloc((void**)&b->status, sizeof(int)) == cudaSuccess &&
               cudaMemset(b->status, 0, sizeof(int)) == cudaSuccess;

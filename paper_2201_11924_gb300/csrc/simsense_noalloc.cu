@@ -121,7 +121,7 @@ extern "C" int simsense_compute_noalloc(const uint8_t* left_u8, const uint8_t* r
     const SelectDebug none{};
     cudaError_t e = launch_census(p, &pair, 1, st);
     if (e == cudaSuccess) e = launch_cost(p, &pair, 1, a.status, st);
-    if (e == cudaSuccess) e = launch_paths(p, &pair, 1, tune, st);
+    if (e == cudaSuccess) e = launch_paths(p, &pair, 1, tune, nullptr, st);
     if (e == cudaSuccess) e = launch_select(p, &pair, 1, tune, none, a.status, st);
     if (e != cudaSuccess) {
         cudaGetLastError();

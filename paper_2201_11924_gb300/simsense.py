@@ -44,7 +44,8 @@ class SimsenseError(RuntimeError):
 class DebugT(ctypes.Structure):
     _fields_ = [("census_left", ctypes.c_void_p), ("census_right", ctypes.c_void_p),
                 ("aggregated", ctypes.c_void_p), ("disparity_int", ctypes.c_void_p),
-                ("disparity", ctypes.c_void_p), ("mask", ctypes.c_void_p)]
+                ("disparity", ctypes.c_void_p), ("mask", ctypes.c_void_p),
+                ("cost", ctypes.c_void_p), ("paths", ctypes.c_void_p)]
 
 
 class CameraT(ctypes.Structure):
@@ -249,6 +250,7 @@ class SimSense:
                  subpixel: bool = True):
         lib = load()
         self.W, self.H, self.D = int(W), int(H), int(D)
+        self.paths = int(paths)
         self._h = ctypes.c_void_p()
         rc = lib.simsense_create(ctypes.byref(self._h), self.W, self.H, self.D,
                                  int(win_w) | (int(win_h) << 8), int(P1), int(P2), int(paths),
@@ -351,8 +353,10 @@ class SimSense:
         self._check(rc, "simsense_compute_host")
         return depth
 
-    def compute_debug(self, left, right, stream=None, aggregated: bool = True):
-        """Depth plus the intermediate results, as a dict of CUDA tensors."""
+    def compute_debug(self, left, right, stream=None, aggregated: bool = True, volumes: bool = False):
+        """Depth plus the intermediate results, as a dict of CUDA tensors;
+        volumes=True adds the cost volume ("cost", H x W x D uint8) and every
+        path's L_r ("paths", paths x H x W x D uint8)."""
         import torch
         dev = left.device
         H, W, D = self.H, self.W, self.D
@@ -366,9 +370,13 @@ class SimSense:
         }
         if aggregated:
             out["aggregated"] = torch.empty((H, W, D), dtype=torch.int16, device=dev)
+        if volumes:
+            out["cost"] = torch.empty((H, W, D), dtype=torch.uint8, device=dev)
+            out["paths"] = torch.empty((self.paths, H, W, D), dtype=torch.uint8, device=dev)
         dbg = DebugT(out["census_left"].data_ptr(), out["census_right"].data_ptr(),
                      out["aggregated"].data_ptr() if aggregated else None,
-                     out["disparity_int"].data_ptr(), out["disparity"].data_ptr(), out["mask"].data_ptr())
+                     out["disparity_int"].data_ptr(), out["disparity"].data_ptr(), out["mask"].data_ptr(),
+                     out["cost"].data_ptr() if volumes else None, out["paths"].data_ptr() if volumes else None)
         shape = (H, W)
         rc = load().simsense_compute_debug(self.handle, _dev_ptr(left, torch.uint8, shape, "left", self.device),
                                            _dev_ptr(right, torch.uint8, shape, "right", self.device),

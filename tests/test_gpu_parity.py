@@ -1,7 +1,7 @@
 """Parity of the CUDA depth stage (through the C ABI) with the CPU oracle.
 
-Bar: census codes, aggregated costs S, integer disparities and validity masks
-bit-exact; fp32 sub-pixel disparity within 1e-4 px and fp32 depth within
+Bar: census codes, the cost volume C, every path's L_r, aggregated costs S,
+integer disparities and validity masks bit-exact; fp32 sub-pixel disparity within 1e-4 px and fp32 depth within
 1e-5 relative of the oracle's fp64 values (the fp32 rounding of one division
 and one sum stays far below both).
 """
@@ -24,13 +24,13 @@ def lib():
     return simsense
 
 
-def _run(lib, wl, left, right, aggregated=True):
+def _run(lib, wl, left, right, aggregated=True, volumes=False):
     import torch
     dev = torch.device("cuda:0")
     with lib.SimSense.from_workload(wl) as m:
         lt = torch.from_numpy(left).to(dev)
         rt = torch.from_numpy(right).to(dev)
-        out = m.compute_debug(lt, rt, aggregated=aggregated)
+        out = m.compute_debug(lt, rt, aggregated=aggregated, volumes=volumes)
         depth2 = m.compute(lt, rt)
         torch.cuda.synchronize()
         assert m.device_status() == 0     # no bounded device-side wait gave up
@@ -58,6 +58,25 @@ def _compare(g, o, wl, check_S=True):
     np.testing.assert_allclose(g["depth"][valid], o["depth"][valid], rtol=DEPTH_RTOL, atol=0)
     # the plain call and the debug call run the same kernels
     np.testing.assert_array_equal(g["depth_plain"], g["depth"])
+
+
+# path directions in the order of the debug dump (the value at p comes from p - r)
+PATH_DIRS = [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, 1), (1, -1), (-1, -1)]
+
+
+def _compare_volumes(g, o, wl):
+    """The cost volume C and every path's L_r bit for bit against the oracle
+    (the cost from the oracle's codes, each L_r from the oracle's path
+    recurrence on that cost), every cell including x - d < 0 and the last
+    disparities of a padded range."""
+    C = oracle.cost(o["codes_left"], o["codes_right"], wl.D, wl.nbits)
+    np.testing.assert_array_equal(g["cost"], C)
+    assert g["paths"].shape[0] == wl.paths
+    for r in range(wl.paths):
+        rx, ry = PATH_DIRS[r]
+        L = oracle.path(C, rx, ry, wl.P1, wl.P2)
+        assert L.max() <= 255
+        np.testing.assert_array_equal(g["paths"][r].astype(np.int32), L, err_msg=f"path r={r} ({rx},{ry})")
 
 
 def _small(name, W, H, D, ww, wh, paths, uniq, lr, sub, P1=7, P2=86, seed=1):
@@ -89,21 +108,28 @@ SMALL_CASES = [
 @pytest.mark.parametrize("wl", SMALL_CASES, ids=lambda w: w.name)
 def test_parity_small(lib, wl):
     p = scenes.make_pair(wl)
-    g = _run(lib, wl, p["left"], p["right"])
+    g = _run(lib, wl, p["left"], p["right"], volumes=True)
     o = _oracle(wl, p["left"], p["right"])
     _compare(g, o, wl)
+    _compare_volumes(g, o, wl)
 
 
 def test_parity_small_workload_320(lib):
     wl = configs.SMALL_320
     p = scenes.make_pair(wl)
-    _compare(_run(lib, wl, p["left"], p["right"]), _oracle(wl, p["left"], p["right"]), wl)
+    g = _run(lib, wl, p["left"], p["right"], volumes=True)
+    o = _oracle(wl, p["left"], p["right"])
+    _compare(g, o, wl)
+    _compare_volumes(g, o, wl)
 
 
 def test_parity_hd_720_full(lib):
     wl = configs.HD_720
     p = scenes.make_pair(wl)
-    _compare(_run(lib, wl, p["left"], p["right"]), _oracle(wl, p["left"], p["right"]), wl)
+    g = _run(lib, wl, p["left"], p["right"], volumes=True)
+    o = _oracle(wl, p["left"], p["right"])
+    _compare(g, o, wl)
+    _compare_volumes(g, o, wl)
 
 
 def test_parity_fhd_1080_full(lib):

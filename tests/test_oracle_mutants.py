@@ -13,10 +13,8 @@ touched.
 
 Every planted mistake changes some result the method defines (none is an
 equivalent rewrite), and every one stays inside its buffers, so a copy fails
-by a wrong value, never by a crash.  Left out on purpose: the constants of
-the named approximations the renderer restates (Schlick's exponent, the
-dielectric F0), which no independent fact fixes, and two changes found to be
-equivalent rewrites: invalid pixels entering the median as -1 instead of 0
+by a wrong value, never by a crash.  Left out on purpose: two changes found
+to be equivalent rewrites: invalid pixels entering the median as -1 instead of 0
 (both sort below every valid disparity) and a rectification fraction of
 256/256 not carrying into the next tap (full weight on that tap gives the
 same value).
@@ -189,6 +187,13 @@ MUTANTS = [
      "if (s < -1.0 || s > 1.0 || w < -1.0 || w > 1.0) return -1.0;",
      "if (s < -2.0 || s > 2.0 || w < -1.0 || w > 1.0) return -1.0;"),
     ("no_ambient_term", "render", "double L = rp->ambient * q->albedo;", "double L = 0.0;"),
+    ("schlick_exponent_4", "render", "double F = F0 + (1.0 - F0) * (m2 * m2 * m1);",
+     "double F = F0 + (1.0 - F0) * (m2 * m2);"),
+    ("schlick_exponent_6", "render", "double F = F0 + (1.0 - F0) * (m2 * m2 * m1);",
+     "double F = F0 + (1.0 - F0) * (m2 * m2 * m2);"),
+    ("dielectric_f0_0_05", "render", "double F0 = 0.04 * (1.0 - q->metallic)",
+     "double F0 = 0.05 * (1.0 - q->metallic)"),
+    ("fresnel_of_n_dot_h", "render", "double vh = dot3(ov, hv);", "double vh = nh;"),
 ]
 
 # the child: point the oracle module at the copy, then run the pins on it

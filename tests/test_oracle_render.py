@@ -8,9 +8,10 @@ the camera centre (closed form), the stereo shift d = f b / Z between the two
 views, projector shadows and nearest hits against an independent ray-sphere
 test, no shadow from behind the projector, Helmholtz reciprocity of the BSDF,
 linearity of the mix in the transmission weight, and the specular highlight of
-a glossy metal sphere at the point facing the light.  Not pinned by any of
-them: the constants of the named approximations (Schlick's exponent 5, the
-dielectric F0 = 0.04), which the oracle restates."""
+a glossy metal sphere at the point facing the light, and the Fresnel factor
+of the specular lobe against the exact Fresnel equations of a dielectric
+(n = 1.5): F0 = 0.04 at normal incidence, Schlick's exponent 5 within its
+deviation from the exact reflectance from grazing to normal incidence."""
 import numpy as np
 import pytest
 
@@ -161,3 +162,87 @@ def test_rectangle_silhouette_is_its_projected_extent():
     inside, outside = (du < 12) & (dv < 6), (du > 12) | (dv > 6)
     assert (lf[inside] >= 400.0 * 0.05 * 0.5 - 1e-9).all()
     assert (lf[outside] == 0.0).all()
+
+
+# --- the Fresnel factor of the specular term ---------------------------------
+#
+# Two renders of the same geometry that differ only in the material isolate the
+# Fresnel factor F of the specular lobe: with transmission 1 (dielectric,
+# metallic 0) the diffuse weight w_d is 0 and F0 is the dielectric one; with
+# metallic 1 and albedo 1, w_d is 0 again and F0 = 1, so F = 1 at every angle.
+# D, G, the light and the geometry are identical, so the ratio of the two
+# unrounded radiances is the dielectric F at cos(theta_d) = v.h of the pixel.
+# The reference is independent of the oracle: the exact Fresnel reflectance
+# of unpolarised light at a dielectric of refractive index 1.5 (the usual
+# value for the dielectrics the F0 = 0.04 convention stands for), from the
+# Fresnel equations.
+
+N_DIELECTRIC = 1.5
+
+
+def _fresnel_exact(c, n=N_DIELECTRIC):
+    """Unpolarised reflectance at incidence cos(theta) = c from the Fresnel
+    equations (s and p averaged)."""
+    s2 = 1.0 - c * c
+    ct = np.sqrt(1.0 - s2 / (n * n))
+    rs = ((c - n * ct) / (c + n * ct)) ** 2
+    rp = ((n * c - ct) / (n * c + ct)) ** 2
+    return 0.5 * (rs + rp)
+
+
+def _fresnel_row(z0, b, Wr=401, f=8.0):
+    """F of every pixel of a one-row render: camera at the origin, projector
+    at (b, 0, 0), a wall z = z0 facing them; returns (cos theta_d, F)."""
+    cx = (Wr - 1) / 2.0
+    pat = np.full((1, 4001), 255, dtype=np.uint8)
+    wall = dict(c=(b / 2.0, 0.0, z0), u=(50.0, 0.0, 0.0), v=(0.0, 50.0, 0.0), roughness=1.0)
+    out = []
+    for mat in (dict(albedo=0.6, metallic=0.0, transmission=1.0), dict(albedo=1.0, metallic=1.0, transmission=0.0)):
+        _, _, lf, _ = oracle.render([oracle.rectangle(**wall, **mat)], pat, Wr, 1, f, cx, 0.0, 0.05,
+                                    (b, 0.0, 0.0), 1.0, 2000.0, 0.0, 1.0, 0.0, 1.0)
+        out.append(lf[0])
+    ok = out[1] > 0
+    ratio = out[0][ok] / out[1][ok]
+    # v.h from the geometry of each pixel's hit point
+    u = np.arange(Wr)[ok]
+    p = np.stack([z0 * (u - cx) / f, np.zeros_like(u, dtype=float), np.full(u.shape, z0)], axis=1)
+    v = -p / np.linalg.norm(p, axis=1, keepdims=True)
+    li = np.array([b, 0.0, 0.0]) - p
+    i = li / np.linalg.norm(li, axis=1, keepdims=True)
+    h = (v + i) / np.linalg.norm(v + i, axis=1, keepdims=True)
+    return np.sum(v * h, axis=1), ratio
+
+
+def test_dielectric_f0_is_the_normal_incidence_reflectance():
+    # projector at the camera: v = i = h for every pixel, so F = F0, which
+    # must equal the reflectance at normal incidence ((n - 1) / (n + 1))^2
+    c, F = _fresnel_row(1.0, 0.0)
+    assert len(F) > 300
+    np.testing.assert_allclose(c, 1.0, atol=1e-12)
+    want = ((N_DIELECTRIC - 1.0) / (N_DIELECTRIC + 1.0)) ** 2
+    np.testing.assert_allclose(F, want, rtol=1e-12)
+    np.testing.assert_allclose(F, _fresnel_exact(np.ones(1))[0], rtol=1e-12)
+
+
+def test_fresnel_factor_follows_the_exact_reflectance_within_schlicks_bound():
+    # Over cos(theta_d) in [0.05, 1], Schlick's form F0 + (1 - F0)(1 - c)^5
+    # stays within 0.036 of the exact reflectance at n = 1.5 (its largest
+    # deviations near grazing incidence); with the exponent 4 or 6 the
+    # deviation reaches 0.10 or 0.055.  The oracle's F must stay within 0.04
+    # at every sampled angle, sampled densely from grazing to normal
+    # incidence, and be monotone in the angle as the exact reflectance is.
+    cs, Fs = [], []
+    for z0, b in ((0.02, 2.0), (0.1, 2.0), (0.3, 1.5), (1.0, 1.0), (3.0, 0.5)):
+        c, F = _fresnel_row(z0, b)
+        cs.append(c)
+        Fs.append(F)
+    c = np.concatenate(cs)
+    F = np.concatenate(Fs)
+    assert c.min() < 0.06 and c.max() > 0.99
+    for lo, hi in ((0.05, 0.2), (0.2, 0.5), (0.5, 0.9), (0.9, 1.0)):
+        assert ((c >= lo) & (c <= hi)).sum() >= 20, (lo, hi)     # every part of the range is sampled
+    sel = c >= 0.05
+    err = np.abs(F[sel] - _fresnel_exact(c[sel]))
+    assert err.max() <= 0.04, err.max()
+    order = np.argsort(c)
+    assert np.all(np.diff(F[order]) <= 1e-12)                    # more grazing -> more reflective
