@@ -151,6 +151,20 @@ def measured_traffic(wl, kernel):
     return nbytes
 
 
+def stage_roofline_frac(wl, ms_per_frame, n_sm, peaks):
+    """The whole stage against its roofline: the slower of the algorithmic
+    HBM bytes at the measured copy peak and the algorithmic integer ops at the
+    derived INT32 peak, over the measured time per frame."""
+    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
+    int_peak = n_sm * INT32_LANES_PER_SM * sm_max * 1e6                  # ops/s
+    bw = float(peaks.get("hbm_gbs", 6800.0)) * 1e9                        # bytes/s
+    t_ops = sum(algorithmic_ops(wl).values()) / int_peak
+    t_bytes = algorithmic_bytes(wl) / bw
+    t_roof = max(t_ops, t_bytes)
+    return {"frac": t_roof / (ms_per_frame / 1e3), "roofline_frames_per_s": 1.0 / t_roof,
+            "bound": "alu" if t_ops >= t_bytes else "hbm", "t_ops_us": t_ops * 1e6, "t_bytes_us": t_bytes * 1e6}
+
+
 def algorithmic_bytes(wl):
     """HBM bytes per frame the method must move: both views in (2 B/px),
     depth out (4 B/px) and one spilled partial-sum volume between the forward
@@ -457,11 +471,11 @@ def run_sim(args):
     return 0
 
 
-def run_batchmix(args):
+def batchmix_measure(steps, warmup, tune_reps=2):
     """The 64-pair batch of uneven sizes ({640x360 D64, 848x480 D96,
     1280x720 D128, 1280x720 D256}, 7x7 census, 8 paths): frames/s of one
     CUDA-graph launch per batch (autotuned per class) against the same pairs
-    as 64 sequential plain calls."""
+    as 64 sequential plain calls (one handle per size, one call per pair)."""
     import torch
     from paper_2201_11924_gb300 import simsense
     dev = torch.device("cuda", 0)
@@ -481,56 +495,78 @@ def run_batchmix(args):
         key = (w.W, w.H, w.D)
         if key not in handles:
             handles[key] = simsense.SimSense.from_workload(w)
+
     def plain_round():
         for i, w in enumerate(wls):
             handles[(w.W, w.H, w.D)].compute(L[i], R[i], Z[i])
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plain_round()
     torch.cuda.synchronize()
     ev0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         plain_round()
     ev1.record(stream)
     torch.cuda.synchronize()
-    plain_ms = ev0.elapsed_time(ev1) / args.steps
+    plain_ms = ev0.elapsed_time(ev1) / steps
+    plain_depth = [z.clone() for z in Z]
     for h in handles.values():
         h.close()
 
     with simsense.SimSenseBatch(wls) as b:
-        tuning = b.tune(L, R, Z, reps=2)
-        for _ in range(args.warmup):
+        t0 = time.perf_counter()
+        tuning = b.tune(L, R, Z, reps=tune_reps)
+        tune_s = time.perf_counter() - t0
+        for _ in range(warmup):
             b.compute(L, R, Z)
         torch.cuda.synchronize()
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             b.compute(L, R, Z)
         ev1.record(stream)
         torch.cuda.synchronize()
-        batch_ms = ev0.elapsed_time(ev1) / args.steps
+        batch_ms = ev0.elapsed_time(ev1) / steps
         status = b.device_status()
         classes = [dict(b.class_info(c)[0], pairs=b.class_info(c)[1], **tuning[c]) for c in range(b.num_classes())]
-    line = {
-        "metric": METRIC, "value": len(wls) / (batch_ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-        "config": {"workload": "batch64_mixed_640x360D64_848x480D96_1280x720D128_1280x720D256_census7x7_8path",
-                   "pairs": len(wls), "cells_per_batch": cells, "graph": True,
-                   "l2": "no flush: every batch streams ~60 GB of path volumes through HBM"},
+    same = all(torch.equal(a, z) for a, z in zip(plain_depth, Z))
+    return {
+        "workload": "batch64_mixed_640x360D64_848x480D96_1280x720D128_1280x720D256_census7x7_8path",
+        "pairs": len(wls), "cells_per_batch": cells, "steps": steps, "warmup": warmup,
+        "value": len(wls) / (batch_ms / 1e3), "unit": UNIT, "ms_per_batch": batch_ms,
         "cells_per_s": cells / (batch_ms / 1e3),
         "plain_value": len(wls) / (plain_ms / 1e3), "plain_ms_per_batch": plain_ms,
-        "speedup_vs_plain": plain_ms / batch_ms, "classes": classes, "device_status": status,
-        "gpu_launches": 4 * len(classes) * args.steps,
+        "speedup_vs_plain": plain_ms / batch_ms, "depth_equals_plain": same,
+        "classes": classes, "tune_s": tune_s, "device_status": status, "graph": True,
+        "gpu_launches_per_batch": 4 * len(classes),
+    }
+
+
+def run_batchmix(args):
+    r = batchmix_measure(args.steps, args.warmup)
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": r["workload"], "pairs": r["pairs"], "cells_per_batch": r["cells_per_batch"],
+                   "graph": True, "l2": "no flush: every batch streams ~60 GB of path volumes through HBM"},
+        "cells_per_s": r["cells_per_s"], "plain_value": r["plain_value"],
+        "plain_ms_per_batch": r["plain_ms_per_batch"], "speedup_vs_plain": r["speedup_vs_plain"],
+        "classes": r["classes"], "device_status": r["device_status"],
+        "gpu_launches": r["gpu_launches_per_batch"] * args.steps,
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_serve(args):
+SERVE_WORKLOAD = "serve_1024cams_poisson_50pct848x480D96_40pct1280x720D128_10pct1920x1080D256"
+
+
+def serve_measure(rate, seconds, sustain, sustain_seconds, slots):
     """Request loop over 1024 cameras (sizes 50% 848x480 D96, 40% 1280x720
     D128, 10% 1920x1080 D256; 7x7 census, 8 paths, uniqueness 15, L/R 1,
     sub-pixel), Poisson arrivals: the continuous-batching server against the
-    same trace served one request at a time (the plain per-request path).
-    Latency = arrival to depth ready, including the frame upload."""
+    same trace served one request at a time (the plain per-request path), at
+    the offered rate and at a rate below the GPU's capacity.  Latency =
+    arrival to depth ready, including the frame upload."""
     import torch
     from paper_2201_11924_gb300 import serve
     dev = torch.device("cuda", 0)
@@ -543,39 +579,84 @@ def run_serve(args):
         if len(frames[key]) < 2:
             p = scenes.make_pair(w)
             frames[key].append((p["left"], p["right"]))
-    srv = serve.DepthServer(cams, frames, slots_per_class=args.serve_slots, device=dev)
+    srv = serve.DepthServer(cams, frames, slots_per_class=slots, device=dev)
     mean_cells = sum(w.cells for w in cams) / len(cams)
     out = {}
-    rates = [("offered", args.serve_rate, args.serve_seconds), ("sustainable", args.serve_sustain, 3.0)]
-    for tag, rate, secs in rates:
+    for tag, r, secs in (("offered", rate, seconds), ("sustainable", sustain, sustain_seconds)):
         for name, seq in (("plain_sequential", True), ("continuous", False)):
             srv.run(serve.poisson_trace(len(cams), 500.0, 0.2, seed=1), sequential=seq)   # warm-up
-            trace = serve.poisson_trace(len(cams), rate, secs, seed=5999)
+            trace = serve.poisson_trace(len(cams), r, secs, seed=5999)
             t0 = time.perf_counter()
             done = srv.run(trace, time_limit=secs + 2.0, sequential=seq)
             wall = time.perf_counter() - t0
             st = serve.latency_stats(done, wall, cams)
-            st.update({"rate_per_s": rate, "offered": len(trace), "offered_per_s": len(trace) / secs,
+            st.update({"rate_per_s": r, "offered": len(trace), "offered_per_s": len(trace) / secs,
                        "offered_cells_per_s": len(trace) * mean_cells / secs,
-                       "backlog_at_stop": srv.backlog, "wall_s": wall, "mean_busy_slots": srv.stats["mean_busy_slots"]})
+                       "backlog_at_stop": srv.backlog, "wall_s": wall, **srv.stats})
             out[f"{tag}_{name}"] = st
-    slots = srv.slot_counts()
+    res = {"workload": SERVE_WORKLOAD, "cameras": len(cams), "rate_per_s": rate, "seconds": seconds,
+           "sustainable_rate_per_s": sustain, "sustainable_seconds": sustain_seconds,
+           "slots": srv.slot_counts(), "hbm": srv.hbm_summary(), "upload": True, **out}
     srv.close()
     c = out["offered_continuous"]
+    res.update({"value": c["served_per_s"], "unit": UNIT, "p50_ms": c["p50_ms"], "p99_ms": c["p99_ms"],
+                "served_cells_per_s": c["served_cells_per_s"],
+                "speedup_vs_sequential_offered": (c["served_per_s"] / out["offered_plain_sequential"]["served_per_s"]
+                                                  if out["offered_plain_sequential"]["served_per_s"] else None),
+                "sustainable_p50_ms": out["sustainable_continuous"]["p50_ms"],
+                "sustainable_p99_ms": out["sustainable_continuous"]["p99_ms"]})
+    return res
+
+
+def run_serve(args):
+    r = serve_measure(args.serve_rate, args.serve_seconds, args.serve_sustain, 3.0, args.serve_slots)
+    c = r["offered_continuous"]
     line = {
-        "metric": METRIC, "value": c["served_per_s"], "unit": UNIT, "n_gpus": 1, "steps": c["served"],
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": c["served"],
         "warmup": 1, "ms_per_step": 1e3 / c["served_per_s"] if c["served_per_s"] else None,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic",
-        "config": {"workload": "serve_1024cams_poisson_50pct848x480D96_40pct1280x720D128_10pct1920x1080D256",
-                   "rate_per_s": args.serve_rate, "seconds": args.serve_seconds, "slots": slots,
-                   "upload": True},
-        "p50_ms": c["p50_ms"], "p99_ms": c["p99_ms"], "served_cells_per_s": c["served_cells_per_s"],
-        "sustainable_p50_ms": out["sustainable_continuous"]["p50_ms"],
-        "sustainable_p99_ms": out["sustainable_continuous"]["p99_ms"], "serve": out,
+        "config": {"workload": SERVE_WORKLOAD, "rate_per_s": args.serve_rate, "seconds": args.serve_seconds,
+                   "slots": r["slots"], "upload": True},
+        "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "served_cells_per_s": r["served_cells_per_s"],
+        "sustainable_p50_ms": r["sustainable_p50_ms"], "sustainable_p99_ms": r["sustainable_p99_ms"],
+        "serve": r,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def plain_measure(wl, steps, warmup, n_sm, peaks, peak_src, n_pairs=2):
+    """Device-timed frames/s of the plain call on one workload (inputs
+    resident in HBM, a few distinct seeded pairs cycled), with its roofline."""
+    import torch
+    from paper_2201_11924_gb300 import simsense
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pairs = [scenes.make_pair(wl, seed=wl.seed + u) for u in range(n_pairs)]
+    lefts = [torch.from_numpy(p["left"]).to(dev) for p in pairs]
+    rights = [torch.from_numpy(p["right"]).to(dev) for p in pairs]
+    depth = torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    with simsense.SimSense.from_workload(wl) as m:
+        for i in range(warmup):
+            m.compute(lefts[i % n_pairs], rights[i % n_pairs], depth)
+        torch.cuda.synchronize()
+        m.set_option(simsense.OPT_PROFILE, 1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(steps):
+            m.compute(lefts[i % n_pairs], rights[i % n_pairs], depth)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        stage_ms, n_prof = m.profile_read()
+        m.set_option(simsense.OPT_PROFILE, 0)
+        status = m.device_status()
+    ms = e0.elapsed_time(e1) / steps
+    roof = roofline_object(wl, stage_ms, n_prof, n_sm, peaks, peak_src)
+    return {"config": workload_config(wl), "steps": steps, "warmup": warmup, "value": 1e3 / ms, "unit": UNIT,
+            "ms_per_step": ms, "cells_per_s": wl.cells * 1e3 / ms,
+            "stage_frac_of_roofline": stage_roofline_frac(wl, ms, n_sm, peaks),
+            "roofline": roof, "device_status": status, "gpu_launches": 4 * steps}
 
 
 def main():
@@ -602,6 +683,8 @@ def main():
     ap.add_argument("--census-cs", action="store_true", help="variant: centre-symmetric census")
     ap.add_argument("--block", default="1x1", help="variant: SGBM block, e.g. 3x3 (1x1 = per-pixel cost)")
     ap.add_argument("--median", type=int, default=0, choices=[0, 3, 5], help="variant: k x k median filter")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="plain line only: skip the small and large workloads, the 64-pair batch and serving")
     ap.add_argument("--batch-pairs", type=int, default=8,
                     help="pairs per batch for the batched sub-measurement of the plain workload")
     args = ap.parse_args()
@@ -748,6 +831,7 @@ def main():
         m.close()
         rep.close()
         return 0
+    m.close()
 
     # roofline of the dominant kernel, from the live stage events
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -759,6 +843,18 @@ def main():
         rate, n, el = cpu_oracle_rate(wl, pairs[0], budget_s=args.cpu_budget_s)
         cpu = {"value": rate / wl.cells, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{n} full-width {wl.W}x90 strips of one pair ({el:.1f} s), per-cell rate extrapolated"}
+
+    # the other configurations of the stage, at N = 1 on this GPU: the small
+    # and the large single pair, the 64-pair uneven batch against 64 plain
+    # calls, and the serving loop at the offered and a sustainable rate
+    extras = {}
+    if world == 1 and not args.no_extras and not variant:
+        extras["workloads"] = {
+            configs.SMALL_320.name: plain_measure(configs.SMALL_320, 2000, 20, n_sm, peaks, peak_src),
+            configs.FHD_1080.name: plain_measure(configs.FHD_1080, 60, 5, n_sm, peaks, peak_src),
+        }
+        extras["batched_cfg3"] = batchmix_measure(steps=3, warmup=2)
+        extras["serve_cfg5"] = serve_measure(args.serve_rate, 2.0, args.serve_sustain, 2.0, args.serve_slots)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -773,13 +869,14 @@ def main():
         "gpu_launches": (4 + int(wl.noise) + int(wl.block != (1, 1)) + int(wl.median > 0)) * args.steps,
         "batched": batched,
         "roofline": roofline,
+        "stage_roofline": stage_roofline_frac(wl, el_ms / args.steps, n_sm, peaks),
         "cpu_baseline": cpu,
         "clocks": clocks,
         "gpu": torch.cuda.get_device_name(dev),
         "host_cores": os.cpu_count(),
+        **extras,
     }
     print(json.dumps(line), flush=True)
-    m.close()
     rep.close()
     return 0
 

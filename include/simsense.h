@@ -411,6 +411,20 @@ size_t simsense_scratch_bytes(simsense_t h);
 /* Release the handle and its scratch memory.  NULL is accepted. */
 int simsense_destroy(simsense_t h);
 
+/*
+ * Completion notice for a request loop (a serving aid; the paper has no
+ * counterpart): once all work enqueued on `stream` before this call has
+ * finished, the 8 bytes of `tag` are written to the file descriptor fd
+ * (typically the write end of a pipe), from the CUDA driver's callback thread.
+ * A loop can then block in poll/select on the read end until its earliest
+ * request is done instead of querying events in a spin.  The write is a single
+ * write of 8 bytes (atomic on a pipe); fd must stay open until the notice has
+ * been written, and a full pipe blocks the stream's later work until it is
+ * read.  SIMSENSE_ERR_INVALID_ARG for fd < 0, SIMSENSE_ERR_CUDA if the host
+ * function cannot be enqueued.
+ */
+int simsense_notify_on_completion(struct CUstream_st* stream, int fd, unsigned long long tag);
+
 /* ------------------------------------------------------------------ batches */
 
 /*

@@ -1,6 +1,8 @@
 // C ABI of libsimsense (declared in include/simsense.h): argument checks,
 // scratch ownership and the launch sequence census -> cost -> paths -> select.
+#include <errno.h>
 #include <math.h>
+#include <unistd.h>
 #include <atomic>
 #include <new>
 
@@ -503,6 +505,48 @@ int simsense_destroy(simsense_t h)
     free_profile(h->prof);
     free_rectify(h);
     delete h;
+    return SIMSENSE_OK;
+}
+
+namespace {
+
+struct Notify {
+    int fd;
+    unsigned long long tag;
+};
+
+// Runs on the CUDA driver's callback thread once the stream reaches it: writes
+// the tag (8 bytes, one atomic pipe write) and makes no CUDA call.
+void CUDART_CB notify_host(void* arg)
+{
+    Notify* n = static_cast<Notify*>(arg);
+    const char* b = reinterpret_cast<const char*>(&n->tag);
+    size_t left = sizeof(n->tag);
+    while (left > 0) {
+        const ssize_t w = write(n->fd, b, left);
+        if (w < 0) {
+            if (errno == EINTR) continue;
+            break;
+        }
+        b += w;
+        left -= (size_t)w;
+    }
+    delete n;
+}
+
+}  // namespace
+
+int simsense_notify_on_completion(struct CUstream_st* stream, int fd, unsigned long long tag)
+{
+    if (fd < 0) return SIMSENSE_ERR_INVALID_ARG;
+    Notify* n = new (std::nothrow) Notify{fd, tag};
+    if (!n) return SIMSENSE_ERR_OOM;
+    const cudaError_t e = cudaLaunchHostFunc((cudaStream_t)stream, notify_host, n);
+    if (e != cudaSuccess) {
+        delete n;
+        cudaGetLastError();
+        return SIMSENSE_ERR_CUDA;
+    }
     return SIMSENSE_OK;
 }
 
