@@ -86,6 +86,15 @@ def roofline_object(wl, stage_ms, n_prof, n_sm, peaks, peak_src):
                 "stage_ms_per_step": {k: v / max(1, n_prof) for k, v in stage_ms.items()},
                 "hbm_algorithmic_bytes_per_frame": algorithmic_bytes(wl),
                 "hbm_peak_gbs": float(peaks.get("hbm_gbs", 6800.0)), "hbm_peak_source": peak_src}
+    total, per = dram_bytes_per_frame(wl)
+    roofline["dram_bytes_per_frame"] = total
+    roofline["dram_bytes_per_kernel"] = per
+    if total is not None:
+        # the whole frame's measured traffic at the copy peak: the shortest
+        # time these bytes allow, against the measured time of the stages
+        frame_s = sum(stage_ms.values()) / 1e3 / max(1, n_prof)
+        roofline["dram_gbs_per_frame_time"] = total / frame_s / 1e9
+        roofline["dram_bound_frames_per_s"] = roofline["hbm_peak_gbs"] * 1e9 / total
     if roofline["traffic"] is not None:
         # the same launch against the HBM roof: its measured DRAM bytes over
         # its live duration (how close its actual traffic runs to the copy peak)
@@ -123,32 +132,46 @@ def algorithmic_ops(wl):
     }
 
 
-# DRAM bytes (read + write) of one launch of the dominant kernel, from one
-# one-kernel ncu capture of the dram__bytes counters, with the SHA-1 of the
-# kernel's source at the time: a changed source reports null.
-MEASURED_TRAFFIC = {
+# DRAM bytes (read, write) of one launch of each kernel, from one one-pass
+# ncu capture of the dram__bytes counters over the four kernels of a frame,
+# with the SHA-1 of each kernel's source at the time: a kernel whose source
+# has changed since reports null.
+MEASURED_DRAM = {
     "1280x720_D128_census7x7_8path": {
-        # (the captured source differed from this one in its opening comment
-        # only: built without line information, both give the same device image)
-        "paths": (548959488 + 887986944, "bcc96c48c1509808a0ec76d4612d28fed94adb16",
-                  "paper_2201_11924_gb300/csrc/sgm_paths.cu"),
+        "census": (1854464, 0, "paper_2201_11924_gb300/csrc/census.cu", "bd6ab68f877a64182190714d9aca0cf5e6ba8d58"),
+        "cost": (14938112, 32452096, "paper_2201_11924_gb300/csrc/cost.cu",
+                 "3d630aa6aa5bd5048f03acb1f0d30450db74a7cc"),
+        "paths": (539111168, 883208704, "paper_2201_11924_gb300/csrc/sgm_paths.cu",
+                  "8ae20832dd6b0c1c4ff5a96895ac76e10cd1a042"),
+        "select": (943819520, 3330560, "paper_2201_11924_gb300/csrc/sgm_select.cu",
+                   "f0ed379d19842bf179830bc86a9d807250941e47"),
     },
 }
 
 
 def measured_traffic(wl, kernel):
+    """(read + write) DRAM bytes of one launch of `kernel`, or None."""
     import hashlib
-    ent = MEASURED_TRAFFIC.get(wl.name, {}).get(kernel)
+    ent = MEASURED_DRAM.get(wl.name, {}).get(kernel)
     if not ent:
         return None
-    nbytes, sha, src = ent
+    rd, wr, src, sha = ent
     try:
         with open(os.path.join(ROOT, src), "rb") as fh:
             if hashlib.sha1(fh.read()).hexdigest() != sha:
                 return None
     except OSError:
         return None
-    return nbytes
+    return rd + wr
+
+
+def dram_bytes_per_frame(wl):
+    """Measured DRAM bytes of all four kernels of a frame (None unless every
+    kernel's capture matches its current source)."""
+    per = {k: measured_traffic(wl, k) for k in ("census", "cost", "paths", "select")}
+    if any(v is None for v in per.values()):
+        return None, per
+    return sum(per.values()), per
 
 
 def stage_roofline_frac(wl, ms_per_frame, n_sm, peaks):

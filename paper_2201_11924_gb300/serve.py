@@ -353,7 +353,12 @@ class DepthServer:
                     self.busy.append(s)
                 if policy == "fifo" and blocked:
                     break                       # the oldest waiting request blocks younger ones
-            # 4. block until the next completion or the next arrival
+            # 4. block until the next completion or the next arrival (or the
+            #    time limit), if there is anything left to wait for
+            if not self.busy and not pending:
+                # done; or requests wait that nothing will ever admit (no
+                # work in flight to free a slot, a camera or memory)
+                break
             now = be.clock() - t0
             timeout = None
             if pending:

@@ -32,8 +32,17 @@ def test_roofline_of_the_1280x720_workload():
     if r["traffic"] is None:
         assert "traffic_gbs" not in r
     else:
-        assert r["traffic"] == 548959488 + 887986944
+        rd, wr = bench.MEASURED_DRAM[wl.name]["paths"][:2]
+        assert r["traffic"] == rd + wr
         assert r["traffic_frac_of_hbm_peak"] == pytest.approx(r["traffic"] / 0.2613e-3 / 1e9 / 6657.6)
+    # the whole frame's measured DRAM bytes: the sum over the four kernels
+    # when every capture matches its source
+    per = r["dram_bytes_per_kernel"]
+    if r["dram_bytes_per_frame"] is not None:
+        assert r["dram_bytes_per_frame"] == sum(per.values())
+        assert r["dram_bound_frames_per_s"] == pytest.approx(6657.6e9 / r["dram_bytes_per_frame"])
+    else:
+        assert any(v is None for v in per.values())
 
 
 def test_roofline_without_recorded_traffic():
