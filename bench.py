@@ -549,8 +549,24 @@ def batchmix_measure(steps, warmup, tune_reps=2):
         torch.cuda.synchronize()
         batch_ms = ev0.elapsed_time(ev1) / steps
         status = b.device_status()
+        same = all(torch.equal(a, z) for a, z in zip(plain_depth, Z))
+        schedule = b.get_schedule()
         classes = [dict(b.class_info(c)[0], pairs=b.class_info(c)[1], **tuning[c]) for c in range(b.num_classes())]
-    same = all(torch.equal(a, z) for a, z in zip(plain_depth, Z))
+        # the other form of the batch, for comparison: per-class launches if
+        # the tuner chose the fused launch, else the fused default
+        other = dict(schedule, fused=0) if schedule["fused"] else dict(fused=1, prefetch=16, keep_paths=1, lag=1,
+                                                                        order=1)
+        b.set_schedule(**other)
+        for _ in range(warmup):
+            b.compute(L, R, Z)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            b.compute(L, R, Z)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        other_ms = ev0.elapsed_time(ev1) / steps
+        same = same and all(torch.equal(a, z) for a, z in zip(plain_depth, Z))
     return {
         "workload": "batch64_mixed_640x360D64_848x480D96_1280x720D128_1280x720D256_census7x7_8path",
         "pairs": len(wls), "cells_per_batch": cells, "steps": steps, "warmup": warmup,
@@ -558,8 +574,12 @@ def batchmix_measure(steps, warmup, tune_reps=2):
         "cells_per_s": cells / (batch_ms / 1e3),
         "plain_value": len(wls) / (plain_ms / 1e3), "plain_ms_per_batch": plain_ms,
         "speedup_vs_plain": plain_ms / batch_ms, "depth_equals_plain": same,
+        "schedule": schedule, "other_form": {"schedule": other, "value": len(wls) / (other_ms / 1e3),
+                                              "ms_per_batch": other_ms},
         "classes": classes, "tune_s": tune_s, "device_status": status, "graph": True,
-        "gpu_launches_per_batch": 4 * len(classes),
+        # census and cost per class, then one persistent launch for the paths
+        # and selection of every pair (fused), or those two per class
+        "gpu_launches_per_batch": 2 * len(classes) + (1 if schedule["fused"] else 2 * len(classes)),
     }
 
 
@@ -573,6 +593,7 @@ def run_batchmix(args):
                    "graph": True, "l2": "no flush: every batch streams ~60 GB of path volumes through HBM"},
         "cells_per_s": r["cells_per_s"], "plain_value": r["plain_value"],
         "plain_ms_per_batch": r["plain_ms_per_batch"], "speedup_vs_plain": r["speedup_vs_plain"],
+        "schedule": r["schedule"], "other_form": r["other_form"], "depth_equals_plain": r["depth_equals_plain"],
         "classes": r["classes"], "device_status": r["device_status"],
         "gpu_launches": r["gpu_launches_per_batch"] * args.steps,
     }

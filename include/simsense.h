@@ -448,10 +448,12 @@ typedef struct simsense_batch* simsense_batch_t;
 
 /*
  * A batch of n pairs of possibly different sizes, disparity ranges and
- * parameters, computed together (the same four stages as simsense_compute,
- * each stage one launch per class of pairs with identical parameters, the
- * classes running concurrently).  Allocates all scratch memory once, on the
- * current device.  Errors as simsense_create.
+ * parameters, computed together (the same four stages as simsense_compute:
+ * census and cost one launch per class of pairs with identical parameters,
+ * the classes running concurrently, then path aggregation and selection of
+ * every pair in one persistent launch, see simsense_batch_schedule_t).
+ * Allocates all scratch memory once, on the current device.  Errors as
+ * simsense_create.
  */
 int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* pairs, int n);
 
@@ -483,9 +485,40 @@ int simsense_batch_get_tuning(simsense_batch_t b, int c, int* prefetch, int* sel
 int simsense_batch_set_tuning(simsense_batch_t b, int c, int prefetch, int select_blocks);
 
 /*
+ * Schedule of the batch (Sec. VI-D's parallel scheme applied to many pairs):
+ *   fused       1 (default): one persistent launch runs the path aggregation
+ *               and the selection of every pair of the batch from a task list
+ *               (census and cost stay one launch per class); 0: every class
+ *               runs its own path and selection launches
+ *   prefetch    pixels of cost in flight per scanline in the fused launch (16)
+ *   keep_paths  fused: 1 = the path volume is stored with the default L2
+ *               policy, so a pair's selection soon after its paths can find
+ *               part of it in L2; 0 = streaming stores
+ *   lag         fused: the selection rows of the k-th pair (in the order
+ *               below) follow the path work of the (k + lag)-th, 1 or 2
+ *   order       fused: pairs as given (0), largest first (1), smallest first
+ *               (2), by W * H * D
+ * Results do not depend on the schedule.  Defaults {1, 16, 1, 1, 1}.
+ * simsense_batch_set_schedule returns SIMSENSE_ERR_INVALID_ARG for values
+ * outside these sets and waits for the device when the task list changes.
+ */
+typedef struct simsense_batch_schedule {
+    int fused;
+    int prefetch;
+    int keep_paths;
+    int lag;
+    int order;
+} simsense_batch_schedule_t;
+
+int simsense_batch_get_schedule(simsense_batch_t b, simsense_batch_schedule_t* out);
+int simsense_batch_set_schedule(simsense_batch_t b, const simsense_batch_schedule_t* sc);
+
+/*
  * Autotuner: for every class, runs its stages with each candidate launch
- * choice `reps` times (1 .. 100) on the given buffers, timed with CUDA
- * events on `stream`, and keeps the fastest.  Synchronises the stream.
+ * choice `reps` times (1 .. 100) on the given buffers, timed with CUDA events
+ * on `stream`, and keeps the fastest; then times whole batches in the
+ * per-class form and in every fused schedule (3 pair orders x 2 lags x 2
+ * store policies) and keeps the fastest schedule.  Synchronises the stream.
  */
 int simsense_batch_tune(simsense_batch_t b, const uint8_t* const* left, const uint8_t* const* right,
                         float* const* depth, int reps, struct CUstream_st* stream);

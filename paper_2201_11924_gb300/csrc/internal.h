@@ -110,6 +110,12 @@ struct Tuning {
     int select_blocks = 1;   // selection kernel: 1 = one 1024-thread block per SM, 2 = two 512-thread blocks
 };
 
+// Limits of the current device (read once per device).
+struct DevLimits {
+    int nsm = 0, optin = 0, per_sm = 0;
+};
+cudaError_t device_limits(DevLimits& out);
+
 // Raises a kernel's dynamic shared-memory limit to `bytes` when a launch needs
 // more than any earlier launch of that kernel on the current device, and on
 // its first call asks for the largest shared-memory carve-out.
@@ -155,6 +161,34 @@ cudaError_t launch_select(const Params& p, const PairPtrs* pairs, int n, const T
 inline size_t path_volume_bytes(const Params& p)
 {
     return (size_t)p.paths * p.W * p.H * p.Dp;
+}
+
+// One pair of a batch as the fused batch kernel reads it (device memory).
+struct FusedPair {
+    const uint8_t* cost;     // H x W x Dp
+    uint8_t* vol;            // H x W x paths x Dp
+    float* depth;            // H x W
+    int W, H, D, Dp, paths, P1, P2;
+    int uniq, lr_max_diff, subpixel;
+    float fb;
+    uint32_t umagic;         // the uniqueness test's multiply-high divisor for 100 - uniq
+    int path_tasks;          // path tasks of the pair (8 work items each)
+};
+
+// Path tasks of a pair in the fused batch kernel, and the shared memory its
+// selection rows need.
+int fused_path_tasks(const Params& p);
+size_t fused_row_bytes(const Params& p);
+// One persistent launch over `ntasks` tasks (int4: kind 0 = path task / 1 =
+// selection row, pair, index) of the pairs in `pairs`; ctl (1 + pairs ints)
+// must be zero at launch.  row_area: the largest fused_row_bytes of the pairs.
+cudaError_t launch_fused(const FusedPair* pairs, const int4* tasks, int ntasks, int* ctl, int* status,
+                         size_t row_area, int keep, cudaStream_t s);
+
+// Multiply-high divisor of the uniqueness test (0 when u is 0 or 99).
+inline uint32_t uniq_magic(int uniq)
+{
+    return (uniq > 0 && uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - uniq)) + 1u : 0u;
 }
 
 // Validation and derived fields shared by every entry point that takes a

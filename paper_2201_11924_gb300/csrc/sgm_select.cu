@@ -24,210 +24,18 @@
 // copies still in flight (again bounded) and ends the block.
 #include <mutex>
 
-#include "internal.h"
+#include "sgm_row.cuh"
 
 namespace simsense {
 namespace {
 
-constexpr int kMaxStages = 4;                // ring depth when shared memory allows
-constexpr uint32_t kMaxPolls = 1u << 22;     // bound on polls of one stage barrier
+using namespace sgm;
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p)
+// Shared-memory bytes of the block: per-row area and the stage barriers.
+template <int NP, int G, int PATHS, int THREADS>
+size_t select_smem(int W, int stages)
 {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-// One thread: expect `bytes` on the stage barrier and start the bulk copy.
-__device__ __forceinline__ void stage_load(uint64_t* bar, void* dst, const void* src, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(smem_addr(bar)), "r"(bytes) : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 :: "r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
-}
-
-// Bounded wait for the phase with the given parity; false if it gave up.
-__device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity)
-{
-    const uint32_t a = smem_addr(bar);
-    for (uint32_t it = 0; it < kMaxPolls; it++) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(a), "r"(parity) : "memory");
-        if (done) return true;
-        if (it > 64) __nanosleep(64);
-    }
-    return false;
-}
-
-// The lane's bytes of one path of one pixel in a stage, as words.
-template <int NP>
-__device__ __forceinline__ void lds_words(uint32_t (&w)[(NP + 1) / 2], const uint8_t* p)
-{
-    if constexpr (NP == 4) {
-        const uint2 v = *reinterpret_cast<const uint2*>(p);
-        w[0] = v.x;
-        w[1] = v.y;
-    } else {   // NP == 3: 6 bytes, 2-byte aligned
-        const uint16_t* q = reinterpret_cast<const uint16_t*>(p);
-        w[0] = (uint32_t)q[0] | ((uint32_t)q[1] << 16);
-        w[1] = q[2];
-    }
-}
-
-// keyR is padded with one word per 32: lanes whose cells map to right pixels
-// 32 apart (lanes 4 apart in a 16-lane group hold disparities 32 apart) then
-// hit different shared-memory banks.
-__device__ __forceinline__ int kr(int xr) { return xr + (xr >> 5); }
-
-// Minimum of a 32-bit value over the G lanes of a group (shuffle butterfly).
-template <int G>
-__device__ __forceinline__ uint32_t group_min(uint32_t v)
-{
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
-// One pixel of the row for one lane group: sum, winner, uniqueness, offers to
-// the right view, parabola.  src is the pixel's first path in the stage.
-// DFULL: D equals the padded range, so every cell is a real disparity;
-// otherwise `pad` marks the lane's padded cells (0xffff halves of the
-// even / odd cell words).
-template <int NP, int G, int PATHS, bool DFULL>
-__device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act, int y, int W, int D,
-                                             int uniq, uint32_t umagic, int subpixel, int gl,
-                                             uint16_t* sw, uint32_t* keyR, uint32_t* info, uint32_t* fit,
-                                             const SelectDebug& dbg, const uint32_t (&pad)[2 * ((NP + 1) / 2)])
-{
-    constexpr int DPT = 2 * NP;
-    constexpr int Dp = G * DPT;
-    constexpr int NW = (NP + 1) / 2;
-    // With two groups per warp, the second one takes its disparity chunks
-    // rotated by half a group, so that the two groups' shared-memory reads of
-    // their two pixels fall on disjoint banks.
-    const int chunk = G == 16 ? (gl + 8 * ((threadIdx.x & 31) / 16)) % 16 : gl;
-    const int d0 = chunk * DPT;
-    const size_t pix = (size_t)y * W + x;
-    // path sums: ev[k] holds cells (4k, 4k+2), od[k] cells (4k+1, 4k+3) as
-    // 16-bit pairs (8 bytes of at most 255 cannot carry out of a half); two
-    // paths per three-input add
-    uint32_t ev[NW], od[NW];
-#pragma unroll
-    for (int k = 0; k < NW; k++) { ev[k] = 0; od[k] = 0; }
-#pragma unroll
-    for (int r = 0; r < PATHS; r += 2) {
-        uint32_t a[NW], b[NW];
-        lds_words<NP>(a, src + r * Dp + d0);
-        lds_words<NP>(b, src + (r + 1) * Dp + d0);
-#pragma unroll
-        for (int k = 0; k < NW; k++) {
-            ev[k] += (a[k] & 0x00ff00ffu) + (b[k] & 0x00ff00ffu);
-            od[k] += __byte_perm(a[k], 0, 0x4341) + __byte_perm(b[k], 0, 0x4341);
-        }
-    }
-    // padded cells d >= D (their path bytes carry no meaning) read as
-    // S = 0xffff: their keys lose to every real cell's (S <= 2040), in the
-    // winner, in the right-view minimum (d = 0 is real for every right
-    // pixel) and, with T capped at 0xffff below, in the uniqueness test
-    if (!DFULL) {
-#pragma unroll
-        for (int k = 0; k < NW; k++) {
-            ev[k] |= pad[2 * k];
-            od[k] |= pad[2 * k + 1];
-        }
-    }
-    // cell j of the lane (d = d0 + j): word j/4, parity j%2, half (j/2)%2
-    uint32_t S[DPT];
-#pragma unroll
-    for (int j = 0; j < DPT; j++) {
-        const uint32_t w = (j & 1) ? od[j >> 2] : ev[j >> 2];
-        S[j] = (j & 2) ? (w >> 16) : (w & 0xffffu);
-    }
-    // winner: minimum key (S << 9) | d over the group, so ties go to the smallest d
-    uint32_t key[DPT];
-    uint32_t kmin = 0xffffffffu;
-#pragma unroll
-    for (int j = 0; j < DPT; j++) {
-        key[j] = (S[j] << 9) + (uint32_t)(d0 + j);
-        kmin = min(kmin, key[j]);
-    }
-    kmin = group_min<G>(kmin);
-    const int ds = (int)(kmin & 511u);
-    const uint32_t smin = kmin >> 9;
-
-    // uniqueness: (100 - u) S(d) < 100 S(d*)  <=>  S(d) < T = ceil(100 S(d*) / (100 - u)),
-    // the division done as a multiply-high by umagic = floor(2^32 / (100 - u)) + 1,
-    // exact for numerators below 2^18; 100 - u = 1 (no magic in 32 bits) divides by one.
-    // The lane compares the minimum over its real cells at least 2 away from d*.
-    bool bad = false;
-    if (uniq > 0) {
-        const uint32_t num = 100u * smin + (uint32_t)(99 - uniq);
-        // capped at 0xffff: every real S is below it, a padded cell equals it
-        const uint32_t T = min(uniq == 99 ? num : __umulhi(num, umagic), 0xffffu);
-        uint32_t m = 0xffffffffu;
-#pragma unroll
-        for (int j = 0; j < DPT; j++) {
-            const int d = d0 + j;
-            if ((uint32_t)(d - ds + 1) > 2u) m = min(m, S[j]);
-        }
-        bad = m < T;
-    }
-    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) / G * G));
-    bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
-
-    if (act) {
-        if constexpr (DPT == 8) {
-            *reinterpret_cast<uint4*>(sw + d0) =
-                make_uint4(__byte_perm(ev[0], od[0], 0x5410), __byte_perm(ev[0], od[0], 0x7632),
-                           __byte_perm(ev[1], od[1], 0x5410), __byte_perm(ev[1], od[1], 0x7632));
-        } else {
-#pragma unroll
-            for (int j = 0; j < DPT; j++) sw[d0 + j] = (uint16_t)S[j];
-        }
-        // offers to the right view: right pixel x - d keeps the minimum key
-        if (x >= Dp - 1) {                     // every cell maps inside the image
-#pragma unroll
-            for (int j = 0; j < DPT; j++)
-                atomicMin(&keyR[kr(x - d0 - j)], key[j]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < DPT; j++) {
-                const int d = d0 + j;
-                if (d <= x) atomicMin(&keyR[kr(x - d)], key[j]);
-            }
-        }
-        if (dbg.aggregated) {
-#pragma unroll
-            for (int j = 0; j < DPT; j++)
-                if (d0 + j < D) dbg.aggregated[pix * D + d0 + j] = (uint16_t)S[j];
-        }
-    }
-    __syncwarp();
-    // the winner and the parabola's samples for the row's epilogue:
-    // info = S(d*) << 16 | failed uniqueness << 15 | parabola fitted << 14 | d*,
-    // fit = S(d*-1) | S(d*+1) << 16
-    if (gl == 0 && act) {
-        const bool para = subpixel && ds >= 1 && ds <= D - 2;
-        info[x] = (smin << 16) | (bad ? 0x8000u : 0u) | (para ? 0x4000u : 0u) | (uint32_t)ds;
-        if (para) fit[x] = (uint32_t)sw[ds - 1] | ((uint32_t)sw[ds + 1] << 16);
-    }
-    __syncwarp();
-}
-
-// Shared-memory bytes of the block: stage ring, barriers, and per-row arrays.
-template <int NP, int G, int THREADS>
-size_t select_smem(int W, int paths, int stages)
-{
-    constexpr int Dp = G * 2 * NP;
-    constexpr int kPix = THREADS / 32 * (32 / G);
-    const size_t ring = (size_t)stages * kPix * paths * Dp;
-    return ring + 8 * kMaxStages + (size_t)(W + W / 32) * 4 + (size_t)W * (4 + 4) + (size_t)kPix * Dp * 2 + 64;
+    return (RowShape<NP, G, PATHS, THREADS>::bytes(W, stages) + 15) / 16 * 16 + 8 * kMaxStages;
 }
 
 // Items are (pair, row); blocks are persistent over them.
@@ -237,154 +45,24 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, ui
                   int lr_max_diff, int subpixel, float fb, SelectDebug dbg, int* __restrict__ status,
                   int kStages, int disp_mode)
 {
-    constexpr int DPT = 2 * NP;
-    constexpr int Dp = G * DPT;
-    constexpr int SPW = 32 / G;                 // pixels a warp takes per stage
-    constexpr int kPix = THREADS / 32 * SPW;    // pixels per stage
     extern __shared__ __align__(128) uint8_t smem[];
-    constexpr size_t pbytes = (size_t)PATHS * Dp;   // one pixel's path costs
-    constexpr size_t stage_bytes = kPix * pbytes;
-    uint8_t* ring = smem;                                              // stages x stage_bytes (multiple of 256)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * stage_bytes);
-    uint16_t* sbuf = reinterpret_cast<uint16_t*>(bars + kMaxStages);   // kPix x Dp, 16-byte aligned
-    uint32_t* keyR = reinterpret_cast<uint32_t*>(sbuf + kPix * Dp);    // W + W/32 (padded)
-    uint32_t* info = keyR + kr(W);                                     // W
-    uint32_t* fit = info + W;                                          // W
+    uint64_t* bars = reinterpret_cast<uint64_t*>(
+        smem + (RowShape<NP, G, PATHS, THREADS>::bytes(W, kStages) + 15) / 16 * 16);
     __shared__ int abort_flag;
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int gl = lane % G, sub = lane / G;
-    const int slot_pix = warp * SPW + sub;      // this group's pixel within a stage
-    // the lane's padded cells (its disparity chunk as select_pixel takes it)
-    uint32_t pad[2 * ((NP + 1) / 2)];
-    {
-        const int chunk = G == 16 ? (gl + 8 * ((threadIdx.x & 31) / 16)) % 16 : gl;
-        const int d0 = chunk * DPT;
-#pragma unroll
-        for (int k = 0; k < (NP + 1) / 2; k++) {
-            pad[2 * k] = (d0 + 4 * k >= D ? 0xffffu : 0u) | (d0 + 4 * k + 2 >= D ? 0xffff0000u : 0u);
-            pad[2 * k + 1] = (d0 + 4 * k + 1 >= D ? 0xffffu : 0u) | (d0 + 4 * k + 3 >= D ? 0xffff0000u : 0u);
-        }
-    }
-    uint16_t* sw = sbuf + slot_pix * Dp;
-    const int nst = (W + kPix - 1) / kPix;      // stages per row
     if (threadIdx.x == 0) {
         for (int k = 0; k < kStages; k++) mbar_init(&bars[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         abort_flag = 0;
     }
     __syncthreads();
-
-    // ring slot and barrier phase of the next stage to consume (stage number
-    // seq of this block lives in slot seq % kStages, phase (seq / kStages) & 1;
-    // both are advanced incrementally)
-    int slot = 0;
-    uint32_t phase = 0;
+    RingPos rp;
     for (int item = blockIdx.x; item < npairs * H; item += gridDim.x) {
         const int pair = item / H, y = item - pair * H;
-        const uint8_t* rowsrc = pt.p[pair].vol + (size_t)y * W * pbytes;
-        float* __restrict__ depth = pt.p[pair].depth;
-        if (threadIdx.x == 0) {
-            for (int k = 0, s = slot; k < kStages && k < nst; k++, s = s + 1 == kStages ? 0 : s + 1) {
-                const int x0 = k * kPix, n = min(kPix, W - x0);
-                stage_load(&bars[s], ring + s * stage_bytes, rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
-            }
-        }
-        for (int i = threadIdx.x; i < kr(W); i += THREADS) keyR[i] = 0xffffffffu;
-        __syncthreads();
-        for (int st = 0; st < nst; st++) {
-            if (!stage_wait(&bars[slot], phase)) abort_flag = 1;
-            const int x = st * kPix + slot_pix;
-            const uint8_t* src = ring + slot * stage_bytes + slot_pix * pbytes;
-            if (D == Dp)
-                select_pixel<NP, G, PATHS, true>(src, x, x < W, y, W, D, uniq, umagic, subpixel, gl, sw, keyR,
-                                                 info, fit, dbg, pad);
-            else
-                select_pixel<NP, G, PATHS, false>(src, x, x < W, y, W, D, uniq, umagic, subpixel, gl, sw, keyR,
-                                                  info, fit, dbg, pad);
-            __syncthreads();                    // everyone is done with this slot
-            if (abort_flag) {
-                if (threadIdx.x == 0) {
-                    if (status) atomicExch(status, SIMSENSE_ERR_TIMEOUT);
-                    // drain the copies still in flight into this block's ring
-                    // (bounded), this stage's own included: its wait may be
-                    // the one that gave up
-                    int s = slot;
-                    uint32_t ph = phase;
-                    for (int j = 0; j < kStages && st + j < nst; j++) {
-                        stage_wait(&bars[s], ph);
-                        if (++s == kStages) { s = 0; ph ^= 1u; }
-                    }
-                }
-                return;
-            }
-            if (threadIdx.x == 0 && st + kStages < nst) {
-                const int x0 = (st + kStages) * kPix, n = min(kPix, W - x0);
-                stage_load(&bars[slot], ring + slot * stage_bytes, rowsrc + (size_t)x0 * pbytes,
-                           (uint32_t)(n * pbytes));
-            }
-            if (++slot == kStages) { slot = 0; phase ^= 1u; }
-        }
-        for (int x = threadIdx.x; x < W; x += THREADS) {
-            const size_t pix = (size_t)y * W + x;
-            const uint32_t in = info[x];
-            const int ds = (int)(in & 511u);
-            int m = (in & 0x8000u) ? 1 : 0;
-            float df = (float)ds;
-            if (in & 0x4000u) {                // parabola through S(d*-1), S(d*), S(d*+1)
-                const uint32_t fv = fit[x];
-                const int sm = (int)(fv & 0xffffu), sp = (int)(fv >> 16), s0 = (int)(in >> 16);
-                df = (float)ds + __fdiv_rn((float)(sm - sp), (float)(2 * (sm + sp - 2 * s0)));
-            }
-            if (lr_max_diff >= 0) {
-                const int xr = x - ds;
-                if (xr < 0) {
-                    m |= 2;
-                } else {
-                    const int dr = (int)(keyR[kr(xr)] & 511u);
-                    const int diff = ds > dr ? ds - dr : dr - ds;
-                    if (diff > lr_max_diff) m |= 2;
-                }
-            }
-            if (!(df > 0.0f)) m |= 4;
-            // disp_mode (a median filter follows): the disparity, 0 when invalid
-            if (disp_mode) depth[pix] = m == 0 ? df : 0.0f;
-            else depth[pix] = m == 0 ? __fdiv_rn(fb, df) : 0.0f;
-            if (dbg.disparity_int) dbg.disparity_int[pix] = (int16_t)ds;
-            if (dbg.disparity) dbg.disparity[pix] = m == 0 ? df : -1.0f;
-            if (dbg.mask) dbg.mask[pix] = (uint8_t)m;
-        }
-        __syncthreads();                        // the row arrays are reused by the next row
+        if (!select_row<NP, G, PATHS, THREADS>(smem, bars, kStages, rp, &abort_flag, pt.p[pair].vol,
+                                               pt.p[pair].depth, y, W, D, uniq, umagic, lr_max_diff, subpixel,
+                                               fb, dbg, status, disp_mode))
+            return;
     }
-}
-
-// Device limits, read once per device.
-struct DevLimits {
-    int nsm = 0, optin = 0, per_sm = 0;
-};
-
-cudaError_t dev_limits(DevLimits& out)
-{
-    constexpr int kMaxDev = 64;
-    static DevLimits cache[kMaxDev];
-    static std::mutex mu;
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lock(mu);
-    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
-    DevLimits& c = cache[dev];
-    if (c.nsm == 0) {
-        e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        if (e != cudaSuccess) {
-            c = DevLimits{};
-            return e;
-        }
-    }
-    out = c;
-    return cudaSuccess;
 }
 
 template <int NP, int G, int PATHS, int THREADS, int N>
@@ -392,21 +70,21 @@ cudaError_t select_launch(const Params& p, const PairTable<N>& pt, int n, const 
                           cudaStream_t s)
 {
     DevLimits lim;
-    cudaError_t e = dev_limits(lim);
+    cudaError_t e = device_limits(lim);
     if (e != cudaSuccess) return e;
     // 1024 / THREADS blocks per SM with the deepest ring that lets them fit
     constexpr int blocks_per_sm = 1024 / THREADS;
     const size_t budget = blocks_per_sm == 1 ? (size_t)lim.optin : (size_t)lim.per_sm / blocks_per_sm - 1024;
     int stages = kMaxStages;
-    while (stages > 2 && select_smem<NP, G, THREADS>(p.W, PATHS, stages) > budget) stages--;
-    const size_t smem = select_smem<NP, G, THREADS>(p.W, PATHS, stages);
+    while (stages > 2 && select_smem<NP, G, PATHS, THREADS>(p.W, stages) > budget) stages--;
+    const size_t smem = select_smem<NP, G, PATHS, THREADS>(p.W, stages);
     if (smem > budget) return cudaErrorInvalidValue;
     auto kernel = sgm_select_kernel<NP, G, PATHS, THREADS, N>;
     e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
     if (e != cudaSuccess) return e;
     const int items = n * p.H;
     const int grid = items < blocks_per_sm * lim.nsm ? items : blocks_per_sm * lim.nsm;   // persistent over rows
-    const uint32_t umagic = (p.uniq > 0 && p.uniq < 99) ? (uint32_t)(0x100000000ull / (uint64_t)(100 - p.uniq)) + 1u : 0u;
+    const uint32_t umagic = uniq_magic(p.uniq);
     kernel<<<grid, THREADS, smem, s>>>(pt, n, p.W, p.H, p.D, p.uniq, umagic, p.lr_max_diff, p.subpixel, p.fb, dbg,
                                        status, stages, p.median > 1 ? 1 : 0);
     return cudaGetLastError();
@@ -441,6 +119,30 @@ cudaError_t select_dp(const Params& p, const PairPtrs* pairs, int n, const Tunin
 }
 
 }  // namespace
+
+cudaError_t device_limits(DevLimits& out)
+{
+    constexpr int kMaxDev = 64;
+    static DevLimits cache[kMaxDev];
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    DevLimits& c = cache[dev];
+    if (c.nsm == 0) {
+        e = cudaDeviceGetAttribute(&c.nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e != cudaSuccess) {
+            c = DevLimits{};
+            return e;
+        }
+    }
+    out = c;
+    return cudaSuccess;
+}
 
 // Raises a kernel's dynamic shared-memory limit when a launch needs more than
 // any earlier launch of that kernel on this device (setting it on every

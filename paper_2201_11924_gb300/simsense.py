@@ -413,6 +413,12 @@ class PairParamsT(ctypes.Structure):
 BATCH_OPT_GRAPH = 1
 
 
+class BatchScheduleT(ctypes.Structure):
+    """simsense_batch_schedule_t: the batch's form and the fused launch's schedule."""
+    _fields_ = [("fused", ctypes.c_int), ("prefetch", ctypes.c_int), ("keep_paths", ctypes.c_int),
+                ("lag", ctypes.c_int), ("order", ctypes.c_int)]
+
+
 def _load_batch():
     lib = load()
     if not getattr(lib, "_batch_ready", False):
@@ -426,6 +432,8 @@ def _load_batch():
         lib.simsense_batch_get_tuning.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(I)]
         lib.simsense_batch_set_tuning.argtypes = [P, I, I, I]
         lib.simsense_batch_tune.argtypes = [P, PP, PP, PP, I, P]
+        lib.simsense_batch_get_schedule.argtypes = [P, ctypes.POINTER(BatchScheduleT)]
+        lib.simsense_batch_set_schedule.argtypes = [P, ctypes.POINTER(BatchScheduleT)]
         lib.simsense_batch_scratch_bytes.argtypes = [P]
         lib.simsense_batch_scratch_bytes.restype = ctypes.c_size_t
         lib.simsense_batch_device_status.argtypes = [P, P]
@@ -434,6 +442,7 @@ def _load_batch():
         for fn in ("simsense_batch_create", "simsense_batch_compute", "simsense_batch_set_option",
                    "simsense_batch_num_classes", "simsense_batch_class_info", "simsense_batch_get_tuning",
                    "simsense_batch_set_tuning", "simsense_batch_tune", "simsense_batch_device_status",
+                   "simsense_batch_get_schedule", "simsense_batch_set_schedule",
                    "simsense_batch_last_cuda_error", "simsense_batch_destroy"):
             getattr(lib, fn).restype = ctypes.c_int
         lib._batch_ready = True
@@ -447,8 +456,10 @@ def pair_params(wl) -> PairParamsT:
 
 class SimSenseBatch:
     """Many pairs of uneven sizes in one call (simsense_batch_*): one CUDA
-    graph of per-class launches, with per-class launch choices that
-    ``tune()`` (the native autotuner) or a tuning cache can set."""
+    graph of per-class census and cost launches and one persistent launch for
+    the paths and selection of every pair (or per-class launches), with a
+    schedule and per-class launch choices that ``tune()`` (the native
+    autotuner) or a tuning cache can set."""
 
     def __init__(self, workloads):
         lib = _load_batch()
@@ -519,7 +530,20 @@ class SimSenseBatch:
         self._check(_load_batch().simsense_batch_set_tuning(self.handle, c, int(prefetch), int(select_blocks)),
                     "simsense_batch_set_tuning")
 
+    def get_schedule(self) -> dict:
+        sc = BatchScheduleT()
+        self._check(_load_batch().simsense_batch_get_schedule(self.handle, ctypes.byref(sc)),
+                    "simsense_batch_get_schedule")
+        return {k: int(getattr(sc, k)) for k, _ in BatchScheduleT._fields_}
+
+    def set_schedule(self, fused: int = 1, prefetch: int = 16, keep_paths: int = 1, lag: int = 1, order: int = 1):
+        sc = BatchScheduleT(int(fused), int(prefetch), int(keep_paths), int(lag), int(order))
+        self._check(_load_batch().simsense_batch_set_schedule(self.handle, ctypes.byref(sc)),
+                    "simsense_batch_set_schedule")
+
     def tune(self, lefts, rights, depths, reps: int = 3, stream=None):
+        """Runs the native autotuner; returns the per-class launch choices
+        (a list) and sets the fastest schedule (``get_schedule()``)."""
         L, R, Z = self._ptrs(lefts, rights, depths)
         self._check(_load_batch().simsense_batch_tune(self.handle, L, R, Z, int(reps), _stream_ptr(stream)),
                     "simsense_batch_tune")

@@ -51,11 +51,13 @@ def _plain(lib, w, l, r):
         return d.cpu().numpy()
 
 
-def test_batch_equals_plain_and_oracle(lib):
+@pytest.mark.parametrize("fused", [1, 0], ids=["fused", "per_class"])
+def test_batch_equals_plain_and_oracle(lib, fused):
     import torch
     pairs, L, R, Z = _inputs(MIX)
     with lib.SimSenseBatch(MIX) as b:
         assert b.num_classes() == len(MIX) - 1
+        b.set_schedule(fused=fused)
         b.compute(L, R, Z)
         torch.cuda.synchronize()
         assert b.device_status() == 0
@@ -100,6 +102,15 @@ def test_tuning_changes_no_result(lib):
         assert len(chosen) == b.num_classes()
         for c, t in enumerate(chosen):
             assert t["prefetch"] in (8, 12, 16) and t["select_blocks"] in (1, 2)
+        sc = b.get_schedule()
+        assert sc["fused"] == 0 or {k: sc[k] for k in ("keep_paths", "lag", "order")} in \
+            [{k: v for k, v in c.items() if k != "fused"} for c in SCHEDULES]
+        for z in Z:
+            z.fill_(0.0)
+        b.compute(L, R, Z)
+        torch.cuda.synchronize()
+        assert all(torch.equal(a, z) for a, z in zip(ref, Z))
+        b.set_schedule(fused=0)                      # the per-class form uses the per-class choices
         for c in range(b.num_classes()):
             for pf, sb in ((8, 1), (16, 2)):
                 b.set_tuning(c, pf, sb)
@@ -108,6 +119,39 @@ def test_tuning_changes_no_result(lib):
                 b.compute(L, R, Z)
                 torch.cuda.synchronize()
                 assert all(torch.equal(a, z) for a, z in zip(ref, Z))
+
+
+SCHEDULES = [dict(fused=1, keep_paths=k, lag=g, order=o) for o in (0, 1, 2) for g in (1, 2) for k in (0, 1)]
+
+
+def test_every_schedule_gives_the_same_depth(lib):
+    # the fused launch's task order, lag and store policy change when each
+    # pair's work runs, never what it computes; the per-class form agrees
+    import torch
+    _, L, R, Z = _inputs(MIX)
+    with lib.SimSenseBatch(MIX) as b:
+        b.set_schedule(fused=0)
+        b.compute(L, R, Z)
+        torch.cuda.synchronize()
+        ref = [z.clone() for z in Z]
+        for sc in SCHEDULES:
+            b.set_schedule(**sc)
+            assert b.get_schedule() == dict(sc, prefetch=16)
+            for z in Z:
+                z.fill_(-5.0)
+            b.compute(L, R, Z)
+            torch.cuda.synchronize()
+            assert b.device_status() == 0, sc
+            assert all(torch.equal(a, z) for a, z in zip(ref, Z)), sc
+
+
+def test_schedule_rejects_values_outside_its_sets(lib):
+    from paper_2201_11924_gb300.simsense import SimsenseError
+    with lib.SimSenseBatch(MIX[:2]) as b:
+        for bad in (dict(fused=2), dict(prefetch=8), dict(keep_paths=3), dict(lag=0), dict(lag=3), dict(order=3)):
+            with pytest.raises(SimsenseError):
+                b.set_schedule(**bad)
+        assert b.get_schedule() == dict(fused=1, prefetch=16, keep_paths=1, lag=1, order=1)
 
 
 def test_more_pairs_than_one_launch_takes(lib):
