@@ -188,6 +188,15 @@ def stage_roofline_frac(wl, ms_per_frame, n_sm, peaks):
             "bound": "alu" if t_ops >= t_bytes else "hbm", "t_ops_us": t_ops * 1e6, "t_bytes_us": t_bytes * 1e6}
 
 
+def batch_roofline_frac(wls, ms_per_batch, n_sm, peaks):
+    """A batch of pairs against the sum of its pairs' rooflines."""
+    t = 0.0
+    for w in wls:
+        r = stage_roofline_frac(w, 1.0, n_sm, peaks)          # t_roof = frac * 1 ms
+        t += r["frac"] * 1e-3
+    return {"frac": t / (ms_per_batch / 1e3), "roofline_ms_per_batch": t * 1e3}
+
+
 def algorithmic_bytes(wl):
     """HBM bytes per frame the method must move: both views in (2 B/px),
     depth out (4 B/px) and one spilled partial-sum volume between the forward
@@ -852,6 +861,8 @@ def main():
         br = [rights[i % n_pairs] for i in range(nb)]
         bd = [torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev) for _ in range(nb)]
         with simsense.SimSenseBatch(bwl) as bt:
+            bt.tune(bl, br, bd, reps=1)            # the native autotuner picks the form and schedule
+            schedule = bt.get_schedule()
             for _ in range(args.warmup):
                 bt.compute(bl, br, bd)
             torch.cuda.synchronize()
@@ -868,7 +879,7 @@ def main():
             status = bt.device_status()
         b_ms = rep.max_over_ranks(b_ms, dev)
         batched = {"value": world * nb * bsteps / (b_ms / 1e3), "unit": UNIT, "pairs_per_batch": nb,
-                   "batches": bsteps, "ms_per_batch": b_ms / bsteps, "graph": True,
+                   "batches": bsteps, "ms_per_batch": b_ms / bsteps, "graph": True, "schedule": schedule,
                    "device_status": status}
 
     if rank != 0:
@@ -881,6 +892,8 @@ def main():
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     peaks, peak_src = _peaks()
     roofline = roofline_object(wl, stage_ms, n_prof, n_sm, peaks, peak_src)
+    if batched is not None:
+        batched["stage_roofline"] = stage_roofline_frac(wl, 1e3 / (batched["value"] / world), n_sm, peaks)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -898,6 +911,8 @@ def main():
             configs.FHD_1080.name: plain_measure(configs.FHD_1080, 60, 5, n_sm, peaks, peak_src),
         }
         extras["batched_cfg3"] = batchmix_measure(steps=3, warmup=2)
+        extras["batched_cfg3"]["stage_roofline"] = batch_roofline_frac(
+            configs.batch_workloads(), extras["batched_cfg3"]["ms_per_batch"], n_sm, peaks)
         extras["serve_cfg5"] = serve_measure(args.serve_rate, 2.0, args.serve_sustain, 2.0, args.serve_slots)
 
     line = {

@@ -175,15 +175,14 @@ struct FusedPair {
     int path_tasks;          // path tasks of the pair (8 work items each)
 };
 
-// Path tasks of a pair in the fused batch kernel, and the shared memory its
-// selection rows need.
+// Path tasks of a pair in the fused batch kernel.
 int fused_path_tasks(const Params& p);
-size_t fused_row_bytes(const Params& p);
 // One persistent launch over `ntasks` tasks (int4: kind 0 = path task / 1 =
 // selection row, pair, index) of the pairs in `pairs`; ctl (1 + pairs ints)
-// must be zero at launch.  row_area: the largest fused_row_bytes of the pairs.
+// must be zero at launch.  cls: the parameters of the batch's ncls classes
+// (the shared memory of the selection rows is sized for the largest).
 cudaError_t launch_fused(const FusedPair* pairs, const int4* tasks, int ntasks, int* ctl, int* status,
-                         size_t row_area, int keep, cudaStream_t s);
+                         const Params* cls, int ncls, int keep, cudaStream_t s);
 
 // Multiply-high divisor of the uniqueness test (0 when u is 0 or 99).
 inline uint32_t uniq_magic(int uniq)

@@ -34,7 +34,7 @@ using namespace sgm;
 
 constexpr int kFusedThreads = 256;
 constexpr int kFusedWarps = kFusedThreads / 32;
-constexpr int kFusedStages = 4;
+constexpr int kFusedStages = 4;               // stage barriers (the ring uses 2 .. 4 of them)
 constexpr uint32_t kMaxDepPolls = 1u << 20;   // bound on polls of a pair's path counter (~1 s)
 
 __device__ __forceinline__ int ld_acquire(const int* p)
@@ -56,26 +56,26 @@ __device__ __forceinline__ void path_task(const FusedPair& q, int item)
 }
 
 template <int NP, int G>
-__device__ __forceinline__ bool row_task(const FusedPair& q, int y, uint8_t* area, uint64_t* bars, RingPos& rp,
-                                         int* abort_flag, int* status)
+__device__ __forceinline__ bool row_task(const FusedPair& q, int y, uint8_t* area, uint64_t* bars, int stages,
+                                         RingPos& rp, int* abort_flag, int* status)
 {
     const SelectDebug none{};
     if (q.paths == 4)
-        return select_row<NP, G, 4, kFusedThreads>(area, bars, kFusedStages, rp, abort_flag, q.vol, q.depth, y, q.W,
-                                                   q.D, q.uniq, q.umagic, q.lr_max_diff, q.subpixel, q.fb, none,
-                                                   status, 0);
-    return select_row<NP, G, 8, kFusedThreads>(area, bars, kFusedStages, rp, abort_flag, q.vol, q.depth, y, q.W, q.D,
+        return select_row<NP, G, 4, kFusedThreads>(area, bars, stages, rp, abort_flag, q.vol, q.depth, y, q.W, q.D,
+                                                   q.uniq, q.umagic, q.lr_max_diff, q.subpixel, q.fb, none, status,
+                                                   0);
+    return select_row<NP, G, 8, kFusedThreads>(area, bars, stages, rp, abort_flag, q.vol, q.depth, y, q.W, q.D,
                                                q.uniq, q.umagic, q.lr_max_diff, q.subpixel, q.fb, none, status, 0);
 }
 
 // tasks[t] = (kind: 0 paths / 1 row, pair, index); ctl[0] = next task,
 // ctl[1 + p] = path tasks of pair p done (all zero at launch); the stage
 // barriers sit at bars_off in dynamic shared memory, after the larger of the
-// path rings and the selection's row area.
+// path rings and the selection's row area (a ring of `stages` stages).
 template <int PF, bool KEEP>
-__global__ void __launch_bounds__(kFusedThreads, 2)
+__global__ void __launch_bounds__(kFusedThreads, 3)
 sgm_fused_kernel(const FusedPair* __restrict__ pairs, const int4* __restrict__ tasks, int ntasks,
-                 int* __restrict__ ctl, int* __restrict__ status, int bars_off)
+                 int* __restrict__ ctl, int* __restrict__ status, int bars_off, int stages)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + bars_off);
@@ -123,10 +123,10 @@ sgm_fused_kernel(const FusedPair* __restrict__ pairs, const int4* __restrict__ t
             if (wait_failed) continue;
             bool ok;
             switch (q.Dp) {
-                case 64: ok = row_task<4, 8>(q, tk.z, smem, bars, rp, &abort_flag, status); break;
-                case 128: ok = row_task<4, 16>(q, tk.z, smem, bars, rp, &abort_flag, status); break;
-                case 192: ok = row_task<3, 32>(q, tk.z, smem, bars, rp, &abort_flag, status); break;
-                default: ok = row_task<4, 32>(q, tk.z, smem, bars, rp, &abort_flag, status); break;
+                case 64: ok = row_task<4, 8>(q, tk.z, smem, bars, stages, rp, &abort_flag, status); break;
+                case 128: ok = row_task<4, 16>(q, tk.z, smem, bars, stages, rp, &abort_flag, status); break;
+                case 192: ok = row_task<3, 32>(q, tk.z, smem, bars, stages, rp, &abort_flag, status); break;
+                default: ok = row_task<4, 32>(q, tk.z, smem, bars, stages, rp, &abort_flag, status); break;
             }
             if (!ok) return;                   // a stage wait gave up: status recorded, ring drained
         }
@@ -134,40 +134,57 @@ sgm_fused_kernel(const FusedPair* __restrict__ pairs, const int4* __restrict__ t
 }
 
 // Shared memory of the selection's row area for the padded range Dp.
-size_t row_bytes(int Dp, int paths, int W)
+size_t row_bytes(int Dp, int paths, int W, int stages)
 {
     switch (Dp) {
-        case 64: return paths == 4 ? RowShape<4, 8, 4, kFusedThreads>::bytes(W, kFusedStages)
-                                   : RowShape<4, 8, 8, kFusedThreads>::bytes(W, kFusedStages);
-        case 128: return paths == 4 ? RowShape<4, 16, 4, kFusedThreads>::bytes(W, kFusedStages)
-                                    : RowShape<4, 16, 8, kFusedThreads>::bytes(W, kFusedStages);
-        case 192: return paths == 4 ? RowShape<3, 32, 4, kFusedThreads>::bytes(W, kFusedStages)
-                                    : RowShape<3, 32, 8, kFusedThreads>::bytes(W, kFusedStages);
-        default: return paths == 4 ? RowShape<4, 32, 4, kFusedThreads>::bytes(W, kFusedStages)
-                                   : RowShape<4, 32, 8, kFusedThreads>::bytes(W, kFusedStages);
+        case 64: return paths == 4 ? RowShape<4, 8, 4, kFusedThreads>::bytes(W, stages)
+                                   : RowShape<4, 8, 8, kFusedThreads>::bytes(W, stages);
+        case 128: return paths == 4 ? RowShape<4, 16, 4, kFusedThreads>::bytes(W, stages)
+                                    : RowShape<4, 16, 8, kFusedThreads>::bytes(W, stages);
+        case 192: return paths == 4 ? RowShape<3, 32, 4, kFusedThreads>::bytes(W, stages)
+                                    : RowShape<3, 32, 8, kFusedThreads>::bytes(W, stages);
+        default: return paths == 4 ? RowShape<4, 32, 4, kFusedThreads>::bytes(W, stages)
+                                   : RowShape<4, 32, 8, kFusedThreads>::bytes(W, stages);
     }
 }
 
+// Launches with the ring depth (2 .. 4 stages) that keeps the most blocks
+// resident per SM, the deeper ring among equals.
 template <int PF, bool KEEP>
 cudaError_t fused_launch(const FusedPair* pairs, const int4* tasks, int ntasks, int* ctl, int* status,
-                         size_t area, cudaStream_t s)
+                         const Params* cls, int ncls, cudaStream_t s)
 {
     DevLimits lim;
     cudaError_t e = device_limits(lim);
     if (e != cudaSuccess) return e;
-    const size_t path_ring = (size_t)kFusedWarps * PF * 512;
-    const size_t bars_off = ((area > path_ring ? area : path_ring) + 15) / 16 * 16;
-    const size_t smem = bars_off + 8 * kFusedStages;
-    if (smem > (size_t)lim.optin) return cudaErrorInvalidValue;
     auto kernel = sgm_fused_kernel<PF, KEEP>;
-    e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kFusedThreads, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidValue;
-    const int grid = per_sm * lim.nsm;
-    kernel<<<grid, kFusedThreads, smem, s>>>(pairs, tasks, ntasks, ctl, status, (int)bars_off);
+    const size_t path_ring = (size_t)kFusedWarps * PF * 512;
+    int best_stages = 0, best_blocks = 0;
+    size_t best_smem = 0, best_off = 0;
+    for (int stages = kFusedStages; stages >= 2; stages--) {
+        size_t area = path_ring;
+        for (int c = 0; c < ncls; c++) {
+            const size_t r = row_bytes(cls[c].Dp, cls[c].paths, cls[c].W, stages);
+            if (r > area) area = r;
+        }
+        const size_t off = (area + 15) / 16 * 16;
+        const size_t smem = off + 8 * kFusedStages;
+        if (smem > (size_t)lim.optin) continue;
+        e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kFusedThreads, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm > best_blocks) {
+            best_blocks = per_sm;
+            best_stages = stages;
+            best_smem = smem;
+            best_off = off;
+        }
+    }
+    if (best_blocks < 1) return cudaErrorInvalidValue;
+    kernel<<<best_blocks * lim.nsm, kFusedThreads, best_smem, s>>>(pairs, tasks, ntasks, ctl, status, (int)best_off,
+                                                                   best_stages);
     return cudaGetLastError();
 }
 
@@ -186,16 +203,11 @@ int fused_path_tasks(const Params& p)
     return (it.total + kFusedWarps - 1) / kFusedWarps;
 }
 
-size_t fused_row_bytes(const Params& p)
-{
-    return row_bytes(p.Dp, p.paths, p.W);
-}
-
 cudaError_t launch_fused(const FusedPair* pairs, const int4* tasks, int ntasks, int* ctl, int* status,
-                         size_t row_area, int keep, cudaStream_t s)
+                         const Params* cls, int ncls, int keep, cudaStream_t s)
 {
-    return keep ? fused_launch<16, true>(pairs, tasks, ntasks, ctl, status, row_area, s)
-                : fused_launch<16, false>(pairs, tasks, ntasks, ctl, status, row_area, s);
+    return keep ? fused_launch<16, true>(pairs, tasks, ntasks, ctl, status, cls, ncls, s)
+                : fused_launch<16, false>(pairs, tasks, ntasks, ctl, status, cls, ncls, s);
 }
 
 }  // namespace simsense

@@ -64,7 +64,7 @@ struct simsense_batch {
     int4* ftasks = nullptr;            // ntasks
     int* fctl = nullptr;               // 1 + n
     int ntasks = 0;
-    size_t row_area = 0;
+    std::vector<Params> cls_params;    // the classes' parameters, for the fused launch
     std::vector<FusedPair> host_fpairs;
     bool fpairs_dirty = true;          // descriptors to upload before the next launch
     cudaStream_t cap = nullptr;        // internal stream the graph is captured on
@@ -156,7 +156,8 @@ cudaError_t enqueue_all(simsense_batch* b, cudaStream_t s)
     if (fused) {
         if (e == cudaSuccess) e = cudaMemsetAsync(b->fctl, 0, sizeof(int) * (1 + (size_t)b->n), s);
         if (e == cudaSuccess)
-            e = launch_fused(b->fpairs, b->ftasks, b->ntasks, b->fctl, b->status, b->row_area, b->sched.keep_paths, s);
+            e = launch_fused(b->fpairs, b->ftasks, b->ntasks, b->fctl, b->status, b->cls_params.data(),
+                             (int)b->cls_params.size(), b->sched.keep_paths, s);
     }
     return e;
 }
@@ -278,8 +279,8 @@ int simsense_batch_create(simsense_batch_t* out, const simsense_pair_params_t* p
         q.umagic = uniq_magic(p.uniq);
         q.path_tasks = fused_path_tasks(p);
         b->ntasks += q.path_tasks + p.H;
-        b->row_area = std::max(b->row_area, fused_row_bytes(p));
     }
+    for (const auto& c : b->classes) b->cls_params.push_back(c.p);
 
     // one allocation: per pair left codes | right codes | cost | path volume,
     // then the fused form's descriptors, task list and counters
