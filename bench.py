@@ -6,9 +6,9 @@
 Prints ONE JSON line (rank 0).  ``value`` is device-timed whole-job
 throughput with the inputs resident in HBM; ``e2e`` is the same metric
 through the host-buffer C-ABI call (pinned host -> device copies, compute,
-depth copied back and read on the host, every step), with two frames in
-flight on two handles and streams as a camera stream runs it (the figure for
-one frame at a time is in the same object); ``roofline`` reports the dominant kernel's
+depth copied back and read on the host, every step), with 2-4 frames in
+flight on as many handles and streams as a camera stream runs it (the figure
+for each number of frames in flight, one included, is in the same object); ``roofline`` reports the dominant kernel's
 achieved integer-op rate (algorithmic ops / its CUDA-event duration) against
 the derived INT32 peak; ``cpu_baseline`` is the CPU oracle timed on a bounded
 sample on this host.  ``--impl reference`` times that oracle alone, on the
@@ -679,6 +679,37 @@ def run_serve(args):
     return 0
 
 
+def batched_measure(wl, nb, batches, warmup, n_sm, peaks, n_pairs=2):
+    """Device-timed frames/s of nb pairs of one workload per batch call
+    (simsense_batch_*, tuned by the native autotuner first), with the
+    whole-stage roofline fraction."""
+    import torch
+    from paper_2201_11924_gb300 import simsense
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pairs = [scenes.make_pair(wl, seed=wl.seed + u) for u in range(n_pairs)]
+    L = [torch.from_numpy(pairs[i % n_pairs]["left"]).to(dev) for i in range(nb)]
+    R = [torch.from_numpy(pairs[i % n_pairs]["right"]).to(dev) for i in range(nb)]
+    Z = [torch.empty((wl.H, wl.W), dtype=torch.float32, device=dev) for _ in range(nb)]
+    stream = torch.cuda.current_stream(dev)
+    with simsense.SimSenseBatch([wl] * nb) as b:
+        b.tune(L, R, Z, reps=1)
+        schedule = b.get_schedule()
+        for _ in range(warmup):
+            b.compute(L, R, Z)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(batches):
+            b.compute(L, R, Z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        status = b.device_status()
+    ms = e0.elapsed_time(e1) / batches
+    return {"pairs_per_batch": nb, "batches": batches, "value": nb * 1e3 / ms, "unit": UNIT,
+            "ms_per_batch": ms, "schedule": schedule, "device_status": status,
+            "stage_roofline": stage_roofline_frac(wl, ms / nb, n_sm, peaks)}
+
+
 def plain_measure(wl, steps, warmup, n_sm, peaks, peak_src, n_pairs=2):
     """Device-timed frames/s of the plain call on one workload (inputs
     resident in HBM, a few distinct seeded pairs cycled), with its roofline."""
@@ -810,46 +841,45 @@ def main():
     el_ms = rep.max_over_ranks(el_ms, dev)
     value = world * args.steps / (el_ms / 1e3)
 
-    # end to end through the host-buffer call, as a camera stream runs it: two
-    # frames in flight (two handles, each on its own stream); every frame
+    # end to end through the host-buffer call, as a camera stream runs it: k
+    # frames in flight (k handles, each on its own stream); every frame
     # uploads its own pinned inputs, computes and downloads its depth, and its
-    # result is read on the host before its handle takes the frame after next
+    # result is read on the host before its handle takes the frame k later
     hl = [torch.from_numpy(p["left"]).pin_memory() for p in pairs]
     hr = [torch.from_numpy(p["right"]).pin_memory() for p in pairs]
-    hd = [torch.empty((wl.H, wl.W), dtype=torch.float32).pin_memory() for _ in range(2)]
-    m2 = simsense.SimSense.from_workload(wl)
-    hs = [m, m2]
-    ss = [stream, torch.cuda.Stream(device=dev)]
-    for i in range(args.warmup):
-        hs[i % 2].compute_host(hl[i % n_pairs], hr[i % n_pairs], hd[i % 2], stream=ss[i % 2])
-    torch.cuda.synchronize()
-    rep.barrier()
     e2e_steps = max(4, min(args.steps, 500))
-    t0 = time.perf_counter()
-    for i in range(e2e_steps):
-        k = i % 2
-        if i >= 2:                               # frame i - 2 on this handle: done, read
+
+    def e2e_run(kf):
+        hd = [torch.empty((wl.H, wl.W), dtype=torch.float32).pin_memory() for _ in range(kf)]
+        extra = [simsense.SimSense.from_workload(wl) for _ in range(kf - 1)]
+        hs = [m] + extra
+        ss = [stream] + [torch.cuda.Stream(device=dev) for _ in range(kf - 1)]
+        for i in range(max(args.warmup, kf)):
+            hs[i % kf].compute_host(hl[i % n_pairs], hr[i % n_pairs], hd[i % kf], stream=ss[i % kf])
+        torch.cuda.synchronize()
+        rep.barrier()
+        t0 = time.perf_counter()
+        for i in range(e2e_steps):
+            k = i % kf
+            if i >= kf:                          # frame i - kf on this handle: done, read
+                ss[k].synchronize()
+                _ = float(hd[k][0, 0])
+            hs[k].compute_host(hl[i % n_pairs], hr[i % n_pairs], hd[k], stream=ss[k])
+        for k in range(kf):
             ss[k].synchronize()
             _ = float(hd[k][0, 0])
-        hs[k].compute_host(hl[i % n_pairs], hr[i % n_pairs], hd[k], stream=ss[k])
-    for k in range(2):
-        ss[k].synchronize()
-        _ = float(hd[k][0, 0])
-    e2e_s = time.perf_counter() - t0
-    m2.close()
-    # the same with one frame in flight (each call waits for the previous)
-    t0 = time.perf_counter()
-    for i in range(e2e_steps):
-        m.compute_host(hl[i % n_pairs], hr[i % n_pairs], hd[0], stream=stream)
-        stream.synchronize()
-        _ = float(hd[0][0, 0])
-    e2e_one = time.perf_counter() - t0
-    e2e_s = rep.max_over_ranks(e2e_s, dev)
-    e2e_one = rep.max_over_ranks(e2e_one, dev)
-    e2e = {"value": world * e2e_steps / e2e_s, "unit": UNIT,
+        el = time.perf_counter() - t0
+        for h in extra:
+            h.close()
+        return rep.max_over_ranks(el, dev)
+
+    by_k = {kf: world * e2e_steps / e2e_run(kf) for kf in (1, 2, 3, 4)}
+    best_k = max((2, 3, 4), key=lambda kf: by_k[kf])
+    e2e = {"value": by_k[best_k], "unit": UNIT,
            "h2d_bytes_per_step": 2 * wl.W * wl.H, "d2h_bytes_per_step": 4 * wl.W * wl.H,
-           "steps": e2e_steps, "frames_in_flight": 2,
-           "one_in_flight_value": world * e2e_steps / e2e_one}
+           "steps": e2e_steps, "frames_in_flight": best_k,
+           "by_frames_in_flight": {str(k): v for k, v in by_k.items()},
+           "one_in_flight_value": by_k[1]}
 
     # the batched form on the same workload: batch_pairs pairs per CUDA-graph launch
     batched = None
@@ -910,6 +940,11 @@ def main():
             configs.SMALL_320.name: plain_measure(configs.SMALL_320, 2000, 20, n_sm, peaks, peak_src),
             configs.FHD_1080.name: plain_measure(configs.FHD_1080, 60, 5, n_sm, peaks, peak_src),
         }
+        # the same workloads as batches of pairs (the throughput form)
+        extras["workloads"][configs.SMALL_320.name]["batched"] = batched_measure(
+            configs.SMALL_320, 64, 20, 3, n_sm, peaks)
+        extras["workloads"][configs.FHD_1080.name]["batched"] = batched_measure(
+            configs.FHD_1080, 8, 6, 2, n_sm, peaks)
         extras["batched_cfg3"] = batchmix_measure(steps=3, warmup=2)
         extras["batched_cfg3"]["stage_roofline"] = batch_roofline_frac(
             configs.batch_workloads(), extras["batched_cfg3"]["ms_per_batch"], n_sm, peaks)

@@ -34,6 +34,14 @@ class FakeBatch:
     def set_tuning(self, c, prefetch, select_blocks):
         self.t[c] = {"prefetch": prefetch, "select_blocks": select_blocks}
 
+    schedule = {"fused": 1, "prefetch": 16, "keep_paths": 1, "lag": 1, "order": 1}
+
+    def get_schedule(self):
+        return dict(self.schedule)
+
+    def set_schedule(self, **sc):
+        self.schedule = dict(sc)
+
 
 CLASSES = [_prm(640, 360, 64, 7, 7, 8), _prm(1280, 720, 128, 7, 7, 8), _prm(1920, 1080, 256, 9, 7, 8)]
 
@@ -70,7 +78,8 @@ def test_another_gpu_does_not_share_entries(tmp_path):
 
 
 @pytest.mark.parametrize("content", ["{not json", json.dumps({"version": 99, "entries": {}}), json.dumps([1, 2]),
-                                     json.dumps({"version": 1, "entries": {"k": {"prefetch": 7, "select_blocks": 1}}})])
+                                     json.dumps({"version": 2, "entries": {"k": {"prefetch": 7, "select_blocks": 1}}}),
+                                     json.dumps({"version": 1, "entries": {"k": {"prefetch": 8, "select_blocks": 1}}})])
 def test_damaged_or_foreign_files_count_as_empty(tmp_path, content):
     path = tmp_path / "tuning.json"
     path.write_text(content)
@@ -86,3 +95,25 @@ def test_only_the_autotuners_choices_are_stored(tmp_path):
     cache = tuning.TuningCache(str(tmp_path / "t.json"))
     with pytest.raises(ValueError):
         cache.put("k", {"prefetch": 10, "select_blocks": 1})
+
+
+def test_the_batch_schedule_round_trips_per_set_of_classes(tmp_path):
+    path = str(tmp_path / "tuning.json")
+    tuned = FakeBatch(CLASSES)
+    tuned.set_schedule(fused=1, prefetch=16, keep_paths=0, lag=2, order=0)
+    cache = tuning.TuningCache(path)
+    tuning.store(tuned, cache, gpu="GB300")
+    cache.save()
+    fresh = FakeBatch(list(reversed(CLASSES)))          # the same classes in another order: the same key
+    tuning.apply(fresh, tuning.TuningCache(path), gpu="GB300")
+    assert fresh.schedule == tuned.schedule
+    other = FakeBatch(CLASSES[:2])                      # other classes: no stored schedule
+    tuning.apply(other, tuning.TuningCache(path), gpu="GB300")
+    assert other.schedule == FakeBatch.schedule
+    with pytest.raises(ValueError):
+        cache.put_schedule("k", {"fused": 1, "prefetch": 8, "keep_paths": 0, "lag": 1, "order": 0})
+    # a damaged schedule entry counts as absent
+    data = json.load(open(path))
+    data["schedules"]["bad"] = {"fused": 3}
+    json.dump(data, open(path, "w"))
+    assert "bad" not in tuning.TuningCache(path).schedules
