@@ -592,6 +592,25 @@ def batchmix_measure(steps, warmup, tune_reps=2):
     }
 
 
+def run_batch(args, wl):
+    """--batch-pairs pairs of one workload per batch call, tuned first."""
+    import torch
+    torch.cuda.set_device(0)
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    peaks, _ = _peaks()
+    r = batched_measure(wl, args.batch_pairs, args.steps, args.warmup, n_sm, peaks)
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {**workload_config(wl), "pairs_per_batch": args.batch_pairs, "graph": True},
+        "schedule": r["schedule"], "stage_roofline": r["stage_roofline"], "device_status": r["device_status"],
+        "gpu_launches": (3 if r["schedule"]["fused"] else 4) * args.steps,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batchmix(args):
     r = batchmix_measure(args.steps, args.warmup)
     line = {
@@ -753,8 +772,9 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-strip-rows", type=int, default=90)
-    ap.add_argument("--mode", default="plain", choices=["plain", "batchmix", "serve", "table2", "sim"],
-                    help="plain: the default contract line; batchmix: the 64-pair mixed batch; "
+    ap.add_argument("--mode", default="plain", choices=["plain", "batch", "batchmix", "serve", "table2", "sim"],
+                    help="plain: the default contract line; batch: --batch-pairs pairs of --workload per "
+                         "batch call (tuned); batchmix: the 64-pair mixed batch; "
                          "table2: the paper's Table 2 workload (960x540, rectified, registered to 1920x1080); "
                          "sim: the whole simulated sensor on the device (render, noise, depth); "
                          "serve: the continuous-batching request loop")
@@ -789,6 +809,8 @@ def main():
         return run_reference(args, wl)
     if args.mode == "batchmix":
         return run_batchmix(args)
+    if args.mode == "batch":
+        return run_batch(args, wl)
     if args.mode == "table2":
         return run_table2(args)
     if args.mode == "sim":
