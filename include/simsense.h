@@ -445,6 +445,16 @@ typedef struct simsense_pair_params {
 typedef struct simsense_batch* simsense_batch_t;
 
 #define SIMSENSE_BATCH_OPT_GRAPH    1     /* 1 (default): capture/replay a CUDA graph; 0: launch directly */
+/*
+ * SIMSENSE_BATCH_OPT_TEST_STALL (value 0/1, default 0): a test of the fused
+ * launch's bounded waits.  While 1, the task list leaves out the path work of
+ * pair 0, so the selection of each of its rows waits for a count that never
+ * completes and gives up after its limit (~0.3 s): the launch records
+ * SIMSENSE_ERR_TIMEOUT (simsense_batch_device_status), pair 0's depth is
+ * undefined, the other pairs are computed as usual and the batch stays
+ * usable.  Nothing faults, traps or hangs.
+ */
+#define SIMSENSE_BATCH_OPT_TEST_STALL 2
 
 /*
  * A batch of n pairs of possibly different sizes, disparity ranges and

@@ -68,7 +68,7 @@ __device__ __forceinline__ bool row_task(const FusedPair& q, int y, uint8_t* are
                                                q.uniq, q.umagic, q.lr_max_diff, q.subpixel, q.fb, none, status, 0);
 }
 
-// tasks[t] = (kind: 0 paths / 1 row, pair, index); ctl[0] = next task,
+// tasks[t] = (kind: 0 paths / 1 row / 2 nothing, pair, index); ctl[0] = next task,
 // ctl[1 + p] = path tasks of pair p done (all zero at launch); the stage
 // barriers sit at bars_off in dynamic shared memory, after the larger of the
 // path rings and the selection's row area (a ring of `stages` stages).
@@ -95,6 +95,7 @@ sgm_fused_kernel(const FusedPair* __restrict__ pairs, const int4* __restrict__ t
         if (t >= ntasks) return;
         const int4 tk = tasks[t];
         const FusedPair& q = pairs[tk.y];
+        if (tk.x == 2) continue;               // a placeholder (the test of the bounded waits)
         if (tk.x == 0) {
             path_task<PF, KEEP>(q, tk.z * kFusedWarps + warp);
             asm volatile("cp.async.wait_all;" ::: "memory");

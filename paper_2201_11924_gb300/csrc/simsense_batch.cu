@@ -67,6 +67,7 @@ struct simsense_batch {
     std::vector<Params> cls_params;    // the classes' parameters, for the fused launch
     std::vector<FusedPair> host_fpairs;
     bool fpairs_dirty = true;          // descriptors to upload before the next launch
+    bool test_drop = false;            // SIMSENSE_BATCH_OPT_TEST_STALL: pair 0's path tasks left out
     cudaStream_t cap = nullptr;        // internal stream the graph is captured on
     cudaEvent_t fork = nullptr;
     cudaEvent_t done = nullptr;
@@ -183,7 +184,8 @@ std::vector<int4> build_tasks(const simsense_batch* b, const simsense_batch_sche
     for (int k = 0; k < b->n; k++) {
         const int i = order[k];
         const int np = b->host_fpairs[i].path_tasks;
-        for (int j = 0; j < np; j++) t.push_back(make_int4(0, i, j, 0));
+        for (int j = 0; j < np; j++)
+            t.push_back(b->test_drop && i == 0 ? make_int4(2, i, j, 0) : make_int4(0, i, j, 0));
         if (k >= sc.lag) rows(order[k - sc.lag]);
     }
     for (int k = std::max(0, b->n - sc.lag); k < b->n; k++) rows(order[k]);
@@ -393,6 +395,10 @@ int simsense_batch_compute(simsense_batch_t b, const uint8_t* const* left, const
     return e == cudaSuccess ? SIMSENSE_OK : fail(b, e);
 }
 
+namespace {
+int apply_schedule(simsense_batch* b, const simsense_batch_schedule_t& sc);
+}  // namespace
+
 int simsense_batch_set_option(simsense_batch_t b, int opt, int value)
 {
     if (!b) return SIMSENSE_ERR_INVALID_ARG;
@@ -400,6 +406,13 @@ int simsense_batch_set_option(simsense_batch_t b, int opt, int value)
         if (value != 0 && value != 1) return SIMSENSE_ERR_INVALID_ARG;
         b->use_graph = value != 0;
         return SIMSENSE_OK;
+    }
+    if (opt == SIMSENSE_BATCH_OPT_TEST_STALL) {
+        if (value != 0 && value != 1) return SIMSENSE_ERR_INVALID_ARG;
+        DeviceGuard g(b->device);
+        if (!g.ok) return fail(b, cudaGetLastError());
+        b->test_drop = value != 0;
+        return apply_schedule(b, b->sched);     // rebuilds the task list
     }
     return SIMSENSE_ERR_INVALID_ARG;
 }

@@ -411,6 +411,7 @@ class PairParamsT(ctypes.Structure):
 
 
 BATCH_OPT_GRAPH = 1
+BATCH_OPT_TEST_STALL = 2   # test of the fused launch's bounded waits (see include/simsense.h)
 
 
 class BatchScheduleT(ctypes.Structure):
@@ -508,6 +509,10 @@ class SimSenseBatch:
 
     def set_graph(self, on: bool):
         self._check(_load_batch().simsense_batch_set_option(self.handle, BATCH_OPT_GRAPH, int(bool(on))),
+                    "simsense_batch_set_option")
+
+    def set_option(self, opt: int, value: int):
+        self._check(_load_batch().simsense_batch_set_option(self.handle, int(opt), int(value)),
                     "simsense_batch_set_option")
 
     def num_classes(self) -> int:

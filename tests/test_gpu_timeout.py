@@ -57,3 +57,42 @@ def test_stall_option_range(lib):
         for bad in (-1, 2):
             with pytest.raises(lib.SimsenseError):
                 m.set_option(lib.OPT_TEST_STALL, bad)
+
+
+def test_fused_batch_wait_gives_up_and_recovers(lib):
+    # the fused batch launch's selection rows wait (bounded) for their pair's
+    # path work; with that work left out of the task list for pair 0
+    # (SIMSENSE_BATCH_OPT_TEST_STALL), every such wait gives up: the launch
+    # reports the timeout, the other pair is computed as usual, and the batch
+    # then computes every pair again
+    import numpy as np
+    import torch
+    from paper_2201_11924_gb300 import configs, scenes
+    mk = lambda name, W, H, D, seed: configs.Workload(
+        name=name, W=W, H=H, D=D, win_w=7, win_h=7, P1=7, P2=86, paths=8, uniq=15, lr_max_diff=1, subpixel=True,
+        f=300.0, baseline=0.055, seed=seed, scene=configs.SMALL_320.scene)
+    wls = [mk("p0", 96, 24, 48, 31), mk("p1", 160, 60, 64, 32)]
+    pairs = [scenes.make_pair(w) for w in wls]
+    L = [torch.from_numpy(p["left"]).cuda() for p in pairs]
+    R = [torch.from_numpy(p["right"]).cuda() for p in pairs]
+    Z = [torch.zeros((w.H, w.W), device="cuda") for w in wls]
+    with lib.SimSenseBatch(wls) as b:
+        b.set_schedule(fused=1)
+        b.compute(L, R, Z)
+        torch.cuda.synchronize()
+        assert b.device_status() == 0
+        ref = [z.clone() for z in Z]
+        b.set_option(lib.BATCH_OPT_TEST_STALL, 1)
+        for z in Z:
+            z.fill_(-2.0)
+        b.compute(L, R, Z)
+        torch.cuda.synchronize()
+        assert b.device_status() == lib.ERR_TIMEOUT
+        assert torch.equal(Z[1], ref[1])
+        assert b.device_status() == 0                    # the status was cleared by the read
+        b.set_option(lib.BATCH_OPT_TEST_STALL, 0)
+        b.compute(L, R, Z)
+        torch.cuda.synchronize()
+        assert b.device_status() == 0
+        assert all(torch.equal(a, z) for a, z in zip(ref, Z))
+        np.testing.assert_array_equal(Z[0].cpu().numpy(), ref[0].cpu().numpy())
