@@ -33,6 +33,8 @@ census_kernel(PairTable<N> pt, int W, int H, int ww_rt, int wh_rt)
 {
     __shared__ uint8_t tile[kTileH * kTileW];
     __shared__ uint8_t tile0[CS ? kTileH * kTileW : 1];   // CS: outside the image = 0
+    pdl_wait();
+    pdl_trigger();
     const int ww = WW > 0 ? WW : ww_rt;
     const int wh = WH > 0 ? WH : wh_rt;
     // fields read one by one: a reference to the parameter array element would
@@ -137,6 +139,8 @@ census_swar_kernel(PairTable<N> pt, int W, int H)
     static_assert(rx <= kSwPad && NG <= 8 && NB <= 8 * (int)sizeof(CodeT), "window");
     __shared__ __align__(16) uint32_t tile[TH * RW];
     __shared__ __align__(16) uint32_t tile0[CS ? TH * RW : 1];
+    pdl_wait();
+    pdl_trigger();
     const int pair = blockIdx.z >> 1;
     const uint8_t* img = (blockIdx.z & 1) ? pt.p[pair].right : pt.p[pair].left;
     CodeT* out = static_cast<CodeT*>((blockIdx.z & 1) ? pt.p[pair].codes_right : pt.p[pair].codes_left);
@@ -270,19 +274,16 @@ cudaError_t census_launch(const Params& p, const PairTable<N>& pt, int n, cudaSt
     // 5x5: 24 / 12 bits
     dim3 sblock(kSwTX, kSwTY);
     dim3 sgrid((p.W + kSwPix - 1) / kSwPix, (p.H + kSwTY - 1) / kSwTY, 2 * n);
+    using WideT = typename std::conditional<CS, uint32_t, uint64_t>::type;
     if (w == 7 && h == 7 && p.wide_codes == !CS)
-        census_swar_kernel<typename std::conditional<CS, uint32_t, uint64_t>::type, 7, 7, CS, N>
-            <<<sgrid, sblock, 0, s>>>(pt, p.W, p.H);
-    else if (w == 9 && h == 7 && p.wide_codes == !CS)
-        census_swar_kernel<typename std::conditional<CS, uint32_t, uint64_t>::type, 9, 7, CS, N>
-            <<<sgrid, sblock, 0, s>>>(pt, p.W, p.H);
-    else if (w == 5 && h == 5 && !p.wide_codes)
-        census_swar_kernel<uint32_t, 5, 5, CS, N><<<sgrid, sblock, 0, s>>>(pt, p.W, p.H);
-    else if (p.wide_codes)
-        census_kernel<uint64_t, 0, 0, CS, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
-    else
-        census_kernel<uint32_t, 0, 0, CS, N><<<grid, block, 0, s>>>(pt, p.W, p.H, w, h);
-    return cudaGetLastError();
+        return launch_pdl(census_swar_kernel<WideT, 7, 7, CS, N>, sgrid, sblock, 0, s, pt, p.W, p.H);
+    if (w == 9 && h == 7 && p.wide_codes == !CS)
+        return launch_pdl(census_swar_kernel<WideT, 9, 7, CS, N>, sgrid, sblock, 0, s, pt, p.W, p.H);
+    if (w == 5 && h == 5 && !p.wide_codes)
+        return launch_pdl(census_swar_kernel<uint32_t, 5, 5, CS, N>, sgrid, sblock, 0, s, pt, p.W, p.H);
+    if (p.wide_codes)
+        return launch_pdl(census_kernel<uint64_t, 0, 0, CS, N>, grid, block, 0, s, pt, p.W, p.H, w, h);
+    return launch_pdl(census_kernel<uint32_t, 0, 0, CS, N>, grid, block, 0, s, pt, p.W, p.H, w, h);
 }
 
 template <int N>

@@ -311,6 +311,8 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
     using CodeT = typename std::conditional<KS == 2, uint64_t, uint32_t>::type;
     using S = TcShape<KS, DP>;
     extern __shared__ __align__(128) uint8_t cost_smem[];
+    pdl_wait();
+    pdl_trigger();
     const uint32_t sbase = smem_u32(cost_smem);
     const uint32_t sS = sbase + S::S_OFF;
     const uint32_t bars = sbase + S::BAR_OFF;
@@ -501,7 +503,9 @@ cudaError_t cost_launch(const Params& p, const PairTable<N>& pt, int n, int* sta
     TileMap tm{p.W, p.H, (p.W + kTileM - 1) / kTileM};
     const int ntiles = n * p.H * tm.tx;
     const int grid = ntiles < sm_count() ? ntiles : sm_count();
-    kernel<<<grid, kCostThreads, S::SMEM, s>>>(pt, tm, ntiles, p.D, p.nbits, km, status, p.test_stall);
+    e = launch_pdl(kernel, dim3(grid), dim3(kCostThreads), S::SMEM, s, pt, tm, ntiles, p.D, p.nbits, km, status,
+                   p.test_stall);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 template <int KS, int N>

@@ -110,6 +110,41 @@ struct Tuning {
     int select_blocks = 1;   // selection kernel: 1 = one 1024-thread block per SM, 2 = two 512-thread blocks
 };
 
+// Programmatic dependent launch.  The main kernels of the stage are launched
+// with programmatic stream serialisation: the next kernel on the stream may
+// be scheduled once every block of the running one has started, and it waits
+// at its first instruction (pdl_wait: griddepcontrol.wait, which returns once
+// the previous kernel has completed and its memory is visible; at once when
+// the kernel was launched without the attribute) before it reads or writes
+// anything.  What overlaps is the launch and the block scheduling of the next
+// kernel with the tail of the running one.
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+// Lets the next kernel be scheduled (called by every block once it runs).
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Limits of the current device (read once per device).
 struct DevLimits {
     int nsm = 0, optin = 0, per_sm = 0;

@@ -59,6 +59,8 @@ sgm_paths_kernel(PairTable<N> pt, int npairs, int W, int H, int P1, int P2, int 
 {
     static_assert(G * 4 * NQ == GH * 4 * NQH, "both layouts cover the same padded range");
     constexpr int SPW = 32 / G, SPWH = 32 / GH;
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const Items it = make_items(W, H, paths, npairs, SPW, SPWH);
     int i = blockIdx.x * (kPathThreads / 32) + (threadIdx.x >> 5);
@@ -104,8 +106,7 @@ cudaError_t paths_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStrea
     auto kernel = sgm_paths_kernel<NQ, G, NQH, GH, PF, N>;
     cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
     if (e != cudaSuccess) return e;
-    kernel<<<blocks, kPathThreads, smem, s>>>(pt, n, p.W, p.H, p.P1, p.P2, p.paths);
-    return cudaGetLastError();
+    return launch_pdl(kernel, dim3(blocks), dim3(kPathThreads), smem, s, pt, n, p.W, p.H, p.P1, p.P2, p.paths);
 }
 
 template <int NQ, int G, int NQH, int GH, int N>

@@ -172,9 +172,15 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
         }
         // offers to the right view: right pixel x - d keeps the minimum key
         if (x >= Dp - 1) {                     // every cell maps inside the image
+            // kr(xr0 - j) = kr(xr0) - j - [j > xr0 mod 32] for j < 32: two
+            // base addresses and a compile-time offset per cell
+            const int xr0 = x - d0;
+            const int c = xr0 & 31;
+            uint32_t* const lo = keyR + kr(xr0);
+            uint32_t* const hi = lo - 1;
 #pragma unroll
             for (int j = 0; j < DPT; j++)
-                atomicMin(&keyR[kr(x - d0 - j)], key[j]);
+                atomicMin((j > c ? hi : lo) - j, key[j]);
         } else {
 #pragma unroll
             for (int j = 0; j < DPT; j++) {

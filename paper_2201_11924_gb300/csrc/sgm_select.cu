@@ -49,6 +49,8 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, ui
     uint64_t* bars = reinterpret_cast<uint64_t*>(
         smem + (RowShape<NP, G, PATHS, THREADS>::bytes(W, kStages) + 15) / 16 * 16);
     __shared__ int abort_flag;
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x == 0) {
         for (int k = 0; k < kStages; k++) mbar_init(&bars[k], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -85,9 +87,8 @@ cudaError_t select_launch(const Params& p, const PairTable<N>& pt, int n, const 
     const int items = n * p.H;
     const int grid = items < blocks_per_sm * lim.nsm ? items : blocks_per_sm * lim.nsm;   // persistent over rows
     const uint32_t umagic = uniq_magic(p.uniq);
-    kernel<<<grid, THREADS, smem, s>>>(pt, n, p.W, p.H, p.D, p.uniq, umagic, p.lr_max_diff, p.subpixel, p.fb, dbg,
-                                       status, stages, p.median > 1 ? 1 : 0);
-    return cudaGetLastError();
+    return launch_pdl(kernel, dim3(grid), dim3(THREADS), smem, s, pt, n, p.W, p.H, p.D, p.uniq, umagic, p.lr_max_diff,
+                      p.subpixel, p.fb, dbg, status, stages, p.median > 1 ? 1 : 0);
 }
 
 template <int NP, int G, int N>
