@@ -744,6 +744,9 @@ def plain_measure(wl, steps, warmup, n_sm, peaks, peak_src, n_pairs=2):
         for i in range(warmup):
             m.compute(lefts[i % n_pairs], rights[i % n_pairs], depth)
         torch.cuda.synchronize()
+        st = m.device_status()
+        if st != 0:
+            raise SystemExit(f"bench: device status {st} after the warm-up steps of {wl.name}")
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for i in range(steps):
@@ -844,6 +847,11 @@ def main():
     for i in range(args.warmup):
         m.compute(lefts[i % n_pairs], rights[i % n_pairs], depth)
     torch.cuda.synchronize()
+    # a bounded device wait that gave up makes every later frame slow and
+    # wrong: stop before the timed region instead of timing it
+    st = m.device_status()
+    if st != 0:
+        raise SystemExit(f"bench: device status {st} after the warm-up steps (a bounded wait gave up)")
 
     sampler = ClockSampler(_bus_id(torch, dev))
     rep.barrier()
