@@ -65,6 +65,17 @@ __device__ __forceinline__ void lds_words(uint32_t (&w)[(NP + 1) / 2], const uin
 // hit different shared-memory banks.
 __device__ __forceinline__ int kr(int xr) { return xr + (xr >> 5); }
 
+// Sum of two pairs of 16-bit integers below 2048 with add.f16x2 (the FMA
+// pipe): as an f16, the bit pattern n < 2048 is n * 2^-24 (subnormal below
+// 1024, exponent field 1 above), so the exact sum is representable and its
+// bit pattern is the integer sum.
+__device__ __forceinline__ uint32_t hadd2_bits(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+
 // Minimum of a 32-bit value over the G lanes of a group (shuffle butterfly).
 template <int G>
 __device__ __forceinline__ uint32_t group_min32(uint32_t v)
@@ -95,20 +106,20 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
     const int d0 = chunk * DPT;
     const size_t pix = (size_t)y * W + x;
     // path sums: ev[k] holds cells (4k, 4k+2), od[k] cells (4k+1, 4k+3) as
-    // 16-bit pairs (8 bytes of at most 255 cannot carry out of a half); two
-    // paths per three-input add
+    // 16-bit halves, accumulated with add.f16x2 (hadd2_bits): a sum of at most
+    // 8 bytes is at most 2040, below 2048, so every partial sum is exact and
+    // the adds run on the FMA pipe, beside the byte extraction and the minima
+    // on the ALU pipe
     uint32_t ev[NW], od[NW];
 #pragma unroll
-    for (int k = 0; k < NW; k++) { ev[k] = 0; od[k] = 0; }
-#pragma unroll
-    for (int r = 0; r < PATHS; r += 2) {
-        uint32_t a[NW], b[NW];
+    for (int r = 0; r < PATHS; r++) {
+        uint32_t a[NW];
         lds_words<NP>(a, src + r * Dp + d0);
-        lds_words<NP>(b, src + (r + 1) * Dp + d0);
 #pragma unroll
         for (int k = 0; k < NW; k++) {
-            ev[k] += (a[k] & 0x00ff00ffu) + (b[k] & 0x00ff00ffu);
-            od[k] += __byte_perm(a[k], 0, 0x4341) + __byte_perm(b[k], 0, 0x4341);
+            const uint32_t e = a[k] & 0x00ff00ffu, o = __byte_perm(a[k], 0, 0x4341);
+            ev[k] = r == 0 ? e : hadd2_bits(ev[k], e);
+            od[k] = r == 0 ? o : hadd2_bits(od[k], o);
         }
     }
     // padded cells d >= D (their path bytes carry no meaning) read as
@@ -133,9 +144,13 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
     uint32_t key[DPT];
     uint32_t kmin = 0xffffffffu;
 #pragma unroll
-    for (int j = 0; j < DPT; j++) {
-        key[j] = (S[j] << 9) + (uint32_t)(d0 + j);
-        kmin = min(kmin, key[j]);
+    for (int j = 0; j < DPT; j++) key[j] = (S[j] << 9) + (uint32_t)(d0 + j);
+    if constexpr (DPT == 8) {
+        kmin = __vimin3_u32(__vimin3_u32(key[0], key[1], key[2]), __vimin3_u32(key[3], key[4], key[5]),
+                            min(key[6], key[7]));
+    } else {
+#pragma unroll
+        for (int j = 0; j < DPT; j++) kmin = min(kmin, key[j]);
     }
     kmin = group_min32<G>(kmin);
     const int ds = (int)(kmin & 511u);

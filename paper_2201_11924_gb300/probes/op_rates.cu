@@ -57,6 +57,18 @@ __device__ __forceinline__ uint32_t op(uint32_t a, uint32_t b, uint32_t c = 0)
     else if constexpr (OP == 42) { d = __vimin3_u16x2(a, b, c); asm volatile("add.u32 %0, %0, %1;\n\tsub.u32 %0, %0, %2;" : "+r"(d) : "r"(b), "r"(c)); }
     else if constexpr (OP == 43) asm volatile("prmt.b32 %0, %1, %2, 0x5432;\n\tlop3.b32 %0, %0, %2, 0x00ff00ff, 0xc0;" : "=r"(d) : "r"(a), "r"(b));
     else if constexpr (OP == 35) { d = __viaddmin_u16x2(a, b, c); asm volatile("min.u16x2 %0, %0, %1;" : "+r"(d) : "r"(b)); }
+    // funnel shift (the pair shifted by one cell across two words) and the
+    // mixes that tell whether f16 minima, funnel shifts and masks share the
+    // pipe of the packed-integer minima
+    else if constexpr (OP == 44) asm volatile("shf.r.wrap.b32 %0, %1, %2, 16;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 45) asm volatile("min.u16x2 %0, %1, %2;\n\tshf.r.wrap.b32 %0, %0, %2, 16;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 46) { d = __vimin3_u16x2(a, b, c); asm volatile("min.f16x2 %0, %0, %1;" : "+r"(d) : "r"(b)); }
+    else if constexpr (OP == 47) asm volatile("lop3.b32 %0, %1, %2, 0x00ff00ff, 0xc0;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 48) asm volatile("min.f16x2 %0, %1, %2;\n\tprmt.b32 %0, %0, %2, 0x5432;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 49) asm volatile("min.f16x2 %0, %1, %2;\n\tshf.r.wrap.b32 %0, %0, %2, 16;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 50) { d = __vimin3_u16x2(a, b, c); asm volatile("min.f16x2 %0, %0, %1;\n\tadd.u32 %0, %0, %1;" : "+r"(d) : "r"(b)); }
+    else if constexpr (OP == 51) asm volatile("add.rn.f16x2 %0, %1, %2;\n\tlop3.b32 %0, %0, %2, 0x00ff00ff, 0xc0;" : "=r"(d) : "r"(a), "r"(b));
+    else if constexpr (OP == 52) asm volatile("add.rn.f16x2 %0, %1, %2;\n\tprmt.b32 %0, %0, %2, 0x4341;" : "=r"(d) : "r"(a), "r"(b));
     return d;
 }
 
@@ -300,6 +312,15 @@ int main()
     run<41>("add + sub (iadd3)", nsm, out, cyc, 2);
     run<42>("vimin3.u16x2 + add + sub", nsm, out, cyc, 3);
     run<43>("prmt + lop3", nsm, out, cyc, 2);
+    run<44>("shf.r.wrap (funnel)", nsm, out, cyc);
+    run<45>("min.u16x2 + shf.r", nsm, out, cyc, 2);
+    run<46>("vimin3.u16x2 + min.f16x2", nsm, out, cyc, 2);
+    run<47>("lop3", nsm, out, cyc);
+    run<48>("min.f16x2 + prmt", nsm, out, cyc, 2);
+    run<49>("min.f16x2 + shf.r", nsm, out, cyc, 2);
+    run<50>("vimin3 + min.f16x2 + add", nsm, out, cyc, 3);
+    run<51>("add.f16x2 + lop3", nsm, out, cyc, 2);
+    run<52>("add.f16x2 + prmt", nsm, out, cyc, 2);
     lat<1>("min.u32", out, cyc);
     lat<2>("min.u16x2", out, cyc);
     lat<4>("prmt", out, cyc);
