@@ -178,7 +178,10 @@ struct TcShape {
     static constexpr int TB = 512 / NBUF;               // columns per accumulator
     static constexpr int N0 = NCOL < 256 ? NCOL : 256;  // the first MMA's N
     static constexpr int N1 = NCOL - N0;                // the second one's (0: none)
-    static constexpr int SROW = DP + 16;                // staging row pitch
+    // staging row pitch: DP + 32 bytes is 8 or 24 words modulo the 32 banks,
+    // which with the lanes' byte offsets (31 - lane) / 4 spreads a warp's 32
+    // word stores over all 32 banks (DP + 16 put two lanes on each bank)
+    static constexpr int SROW = DP + 32;
     static constexpr int OPS = (kTileM + NCOL) * RB;    // one operand buffer (A then B)
     static constexpr int S_OFF = 2 * OPS;               // staging rows of the two epilogue groups
     static constexpr int BAR_OFF = S_OFF + 2 * kTileM * SROW;
