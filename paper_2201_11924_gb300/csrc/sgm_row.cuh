@@ -49,7 +49,13 @@ __device__ __forceinline__ bool stage_wait(uint64_t* bar, uint32_t parity)
 template <int NP>
 __device__ __forceinline__ void lds_words(uint32_t (&w)[(NP + 1) / 2], const uint8_t* p)
 {
-    if constexpr (NP == 4) {
+    if constexpr (NP == 8) {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        w[0] = v.x;
+        w[1] = v.y;
+        w[2] = v.z;
+        w[3] = v.w;
+    } else if constexpr (NP == 4) {
         const uint2 v = *reinterpret_cast<const uint2*>(p);
         w[0] = v.x;
         w[1] = v.y;
@@ -149,8 +155,10 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
         kmin = __vimin3_u32(__vimin3_u32(key[0], key[1], key[2]), __vimin3_u32(key[3], key[4], key[5]),
                             min(key[6], key[7]));
     } else {
+        kmin = key[0];
 #pragma unroll
-        for (int j = 0; j < DPT; j++) kmin = min(kmin, key[j]);
+        for (int j = 1; j + 1 < DPT; j += 2) kmin = __vimin3_u32(kmin, key[j], key[j + 1]);
+        if constexpr (DPT % 2 == 0) kmin = min(kmin, key[DPT - 1]);
     }
     kmin = group_min32<G>(kmin);
     const int ds = (int)(kmin & 511u);
@@ -177,10 +185,12 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
     bad = (__ballot_sync(0xffffffffu, bad) & gmask) != 0;
 
     if (act) {
-        if constexpr (DPT == 8) {
-            *reinterpret_cast<uint4*>(sw + d0) =
-                make_uint4(__byte_perm(ev[0], od[0], 0x5410), __byte_perm(ev[0], od[0], 0x7632),
-                           __byte_perm(ev[1], od[1], 0x5410), __byte_perm(ev[1], od[1], 0x7632));
+        if constexpr (DPT % 8 == 0) {
+#pragma unroll
+            for (int k = 0; k < DPT / 4; k += 2)
+                *reinterpret_cast<uint4*>(sw + d0 + 4 * k) =
+                    make_uint4(__byte_perm(ev[k], od[k], 0x5410), __byte_perm(ev[k], od[k], 0x7632),
+                               __byte_perm(ev[k + 1], od[k + 1], 0x5410), __byte_perm(ev[k + 1], od[k + 1], 0x7632));
         } else {
 #pragma unroll
             for (int j = 0; j < DPT; j++) sw[d0 + j] = (uint16_t)S[j];
