@@ -252,24 +252,30 @@ struct RowShape {
 
 // Position of a block in its stage ring: stage number seq of the block lives
 // in slot seq % stages with barrier phase (seq / stages) & 1, both advanced
-// incrementally from row to row.
+// incrementally from row to row.  ahead: stages of the block's next row whose
+// copies the previous row already started (thread 0's count).
 struct RingPos {
     int slot = 0;
     uint32_t phase = 0;
+    int ahead = 0;
 };
 
 // One image row y of one pair, by the whole block: every pixel's sum, winner,
 // uniqueness and offers to the right view stage by stage, then the row
 // epilogue (left-right check, parabola, depth).  area: RowShape::bytes of
 // shared memory; bars: `stages` initialised stage barriers; abort_flag: a
-// shared word, 0 on entry.  Returns false if a stage wait gave up: the status
-// word then holds SIMSENSE_ERR_TIMEOUT, the copies in flight have been
-// drained (bounded) and the block must not touch the ring again.
+// shared word, 0 on entry.  next_src: the path bytes of the row this block
+// selects next (same W and layout), or null: as this row's last stages free
+// their slots, the copies of the next row's first stages start, so that the
+// row epilogue and the next row's start do not wait for DRAM.  Returns false
+// if a stage wait gave up: the status word then holds SIMSENSE_ERR_TIMEOUT,
+// the copies in flight have been drained (bounded) and the block must not
+// touch the ring again.
 template <int NP, int G, int PATHS, int THREADS>
 __device__ bool select_row(uint8_t* area, uint64_t* bars, int stages, RingPos& rp, int* abort_flag,
                            const uint8_t* __restrict__ vol, float* __restrict__ depth, int y, int W, int D, int uniq,
                            uint32_t umagic, int lr_max_diff, int subpixel, float fb, const SelectDebug& dbg,
-                           int* __restrict__ status, int disp_mode)
+                           int* __restrict__ status, int disp_mode, const uint8_t* next_src = nullptr)
 {
     using RS = RowShape<NP, G, PATHS, THREADS>;
     constexpr int DPT = RS::DPT;
@@ -303,9 +309,15 @@ __device__ bool select_row(uint8_t* area, uint64_t* bars, int stages, RingPos& r
     const uint8_t* rowsrc = vol + (size_t)y * W * pbytes;
     int slot = rp.slot;
     uint32_t phase = rp.phase;
+    // thread 0's count of this row's stages whose copies have started, and
+    // of the next row's
+    int issued = 0, next_issued = 0;
     if (threadIdx.x == 0) {
-        for (int k = 0, s = slot; k < stages && k < nst; k++, s = s + 1 == stages ? 0 : s + 1) {
-            const int x0 = k * kPix, n = min(kPix, W - x0);
+        issued = min(rp.ahead, nst);
+        int s = slot + issued;
+        s = s >= stages ? s - stages : s;
+        for (; issued < stages && issued < nst; issued++, s = s + 1 == stages ? 0 : s + 1) {
+            const int x0 = issued * kPix, n = min(kPix, W - x0);
             stage_load(&bars[s], ring + s * stage_bytes, rowsrc + (size_t)x0 * pbytes, (uint32_t)(n * pbytes));
         }
     }
@@ -330,22 +342,35 @@ __device__ bool select_row(uint8_t* area, uint64_t* bars, int stages, RingPos& r
                 // the one that gave up
                 int s = slot;
                 uint32_t ph = phase;
-                for (int j = 0; j < stages && st + j < nst; j++) {
+                for (int j = st; j < issued + next_issued; j++) {
                     stage_wait(&bars[s], ph);
                     if (++s == stages) { s = 0; ph ^= 1u; }
                 }
             }
             return false;
         }
-        if (threadIdx.x == 0 && st + stages < nst) {
-            const int x0 = (st + stages) * kPix, n = min(kPix, W - x0);
-            stage_load(&bars[slot], ring + slot * stage_bytes, rowsrc + (size_t)x0 * pbytes,
-                       (uint32_t)(n * pbytes));
+        if (threadIdx.x == 0) {
+            // the slot just freed takes the stage `stages` ahead: of this
+            // row while it has one, else of the next row (when this row has
+            // fewer stages than the ring, the sequence positions of the two
+            // rows' stages do not line up, and nothing is fetched ahead)
+            if (issued < nst) {
+                const int x0 = issued * kPix, n = min(kPix, W - x0);
+                stage_load(&bars[slot], ring + slot * stage_bytes, rowsrc + (size_t)x0 * pbytes,
+                           (uint32_t)(n * pbytes));
+                issued++;
+            } else if (next_src && next_issued < nst && st + stages == nst + next_issued) {
+                const int x0 = next_issued * kPix, n = min(kPix, W - x0);
+                stage_load(&bars[slot], ring + slot * stage_bytes, next_src + (size_t)x0 * pbytes,
+                           (uint32_t)(n * pbytes));
+                next_issued++;
+            }
         }
         if (++slot == stages) { slot = 0; phase ^= 1u; }
     }
     rp.slot = slot;
     rp.phase = phase;
+    rp.ahead = next_issued;
     for (int x = threadIdx.x; x < W; x += THREADS) {
         const size_t pix = (size_t)y * W + x;
         const uint32_t in = info[x];

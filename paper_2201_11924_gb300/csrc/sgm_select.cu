@@ -58,11 +58,18 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, ui
     }
     __syncthreads();
     RingPos rp;
+    constexpr size_t pbytes = RowShape<NP, G, PATHS, THREADS>::pbytes;
     for (int item = blockIdx.x; item < npairs * H; item += gridDim.x) {
         const int pair = item / H, y = item - pair * H;
+        const int next = item + gridDim.x;
+        const uint8_t* next_src = nullptr;
+        if (next < npairs * H) {
+            const int np = next / H, ny = next - np * H;
+            next_src = pt.p[np].vol + (size_t)ny * W * pbytes;
+        }
         if (!select_row<NP, G, PATHS, THREADS>(smem, bars, kStages, rp, &abort_flag, pt.p[pair].vol,
                                                pt.p[pair].depth, y, W, D, uniq, umagic, lr_max_diff, subpixel,
-                                               fb, dbg, status, disp_mode))
+                                               fb, dbg, status, disp_mode, next_src))
             return;
     }
 }
