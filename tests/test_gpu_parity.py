@@ -102,6 +102,12 @@ SMALL_CASES = [
     _small("max_P2", 90, 20, 70, 9, 7, 8, 50, 1, True, P1=0, P2=193, seed=11),
     _small("win_15x3", 70, 25, 40, 15, 3, 8, 0, 1, True, seed=12),
     _small("win_1x1", 30, 10, 8, 3, 1, 4, 0, 1, True, seed=13),
+    # long rows with slowly forgetting paths: with P1 = 0 and the largest P2,
+    # a row's path restarted in its middle reaches the true state only 23-68
+    # pixels later (by the oracle's recurrence); and a D = 96 (padded to 128)
+    # row of 700 pixels
+    _small("split_rows_slow_agreement", 520, 24, 64, 7, 7, 8, 10, 1, True, P1=0, P2=193, seed=21),
+    _small("split_rows_D128", 700, 16, 96, 9, 7, 8, 10, 1, True, P1=1, P2=150, seed=23),
 ]
 
 
