@@ -136,31 +136,48 @@ def algorithmic_ops(wl):
 # ncu capture of the dram__bytes counters over the four kernels of a frame,
 # with the SHA-1 of each kernel's source at the time: a kernel whose source
 # has changed since reports null.
+# Per-kernel DRAM bytes of one launch (read, write) from a one-pass ncu
+# capture of the default workload, keyed on the SHA-1 of the kernel's sources
+# (its .cu file and the device headers it includes, concatenated in this
+# order) at the time of the capture: a kernel whose sources changed since
+# reports None.
+KERNEL_SOURCES = {
+    "census": ("paper_2201_11924_gb300/csrc/census.cu",),
+    "cost": ("paper_2201_11924_gb300/csrc/cost.cu",),
+    "paths": ("paper_2201_11924_gb300/csrc/sgm_paths.cu", "paper_2201_11924_gb300/csrc/sgm_walk.cuh",
+              "paper_2201_11924_gb300/csrc/simd.cuh"),
+    "select": ("paper_2201_11924_gb300/csrc/sgm_select.cu", "paper_2201_11924_gb300/csrc/sgm_row.cuh"),
+}
 MEASURED_DRAM = {
     "1280x720_D128_census7x7_8path": {
-        "census": (1854464, 0, "paper_2201_11924_gb300/csrc/census.cu", "bd6ab68f877a64182190714d9aca0cf5e6ba8d58"),
-        "cost": (14938112, 32452096, "paper_2201_11924_gb300/csrc/cost.cu",
-                 "3d630aa6aa5bd5048f03acb1f0d30450db74a7cc"),
-        "paths": (539111168, 883208704, "paper_2201_11924_gb300/csrc/sgm_paths.cu",
-                  "8ae20832dd6b0c1c4ff5a96895ac76e10cd1a042"),
-        "select": (943819520, 3330560, "paper_2201_11924_gb300/csrc/sgm_select.cu",
-                   "f0ed379d19842bf179830bc86a9d807250941e47"),
+        "census": (1854976, 0, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
+        "cost": (14914816, 31962368, "5f38f3e5f9a7f8ecefb41e81bd830ba85ab2e586"),
+        "paths": (536578304, 884640000, "7a3ca98f38d4c2d2000bd762f622c6fa33b96e46"),
+        "select": (943763712, 3276544, "9ff7efd5fe90fb3ca2008e966dd646ec5b564c1f"),
     },
 }
 
 
+def kernel_source_sha(kernel):
+    """SHA-1 of the kernel's sources, concatenated (None if one is missing)."""
+    import hashlib
+    h = hashlib.sha1()
+    try:
+        for src in KERNEL_SOURCES[kernel]:
+            with open(os.path.join(ROOT, src), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    return h.hexdigest()
+
+
 def measured_traffic(wl, kernel):
     """(read + write) DRAM bytes of one launch of `kernel`, or None."""
-    import hashlib
     ent = MEASURED_DRAM.get(wl.name, {}).get(kernel)
     if not ent:
         return None
-    rd, wr, src, sha = ent
-    try:
-        with open(os.path.join(ROOT, src), "rb") as fh:
-            if hashlib.sha1(fh.read()).hexdigest() != sha:
-                return None
-    except OSError:
+    rd, wr, sha = ent
+    if kernel_source_sha(kernel) != sha:
         return None
     return rd + wr
 
