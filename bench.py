@@ -150,10 +150,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_DRAM = {
     "1280x720_D128_census7x7_8path": {
-        "census": (1854976, 0, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
-        "cost": (14914816, 31962368, "5f38f3e5f9a7f8ecefb41e81bd830ba85ab2e586"),
-        "paths": (536578304, 884640000, "7a3ca98f38d4c2d2000bd762f622c6fa33b96e46"),
-        "select": (943763712, 3276544, "9ff7efd5fe90fb3ca2008e966dd646ec5b564c1f"),
+        "census": (1855744, 1024, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
+        "cost": (14936576, 31500800, "52eb3a6f1b23f3163bbdc1692ebd48afd1e09980"),
+        "paths": (536728064, 884464128, "798c2386b591a8b3b63ad3976906ae4877a22974"),
+        "select": (943777792, 3174912, "9ff7efd5fe90fb3ca2008e966dd646ec5b564c1f"),
     },
 }
 

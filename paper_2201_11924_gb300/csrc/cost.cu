@@ -352,7 +352,7 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
     if (warp >= kEpiWarps && warp < kIssuerWarp) {
         // ---- producers: thread p expands left pixel x0 + p and right rows p + 128 j
         const int p = tid - 32 * kEpiWarps;
-        CodeT cl = 0, cr[S::RPT], nl = 0, nr[S::RPT];
+        CodeT cl = 0, cr[S::RPT], nl = 0, nr[S::RPT], ml = 0, mr[S::RPT];
         TileMap::Pos q = tm.at(t0 < t1 ? t0 : 0);
         auto fetch = [&](const TileMap::Pos& at, CodeT& l, CodeT (&r)[S::RPT]) {
             const CodeT* rowL = static_cast<const CodeT*>(pt.p[at.pair].codes_left) + (size_t)at.y * tm.W;
@@ -365,11 +365,18 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
             }
         };
         if (t0 < t1) fetch(q, cl, cr);
+        if (t0 + 1 < t1) {
+            tm.step(q);
+            fetch(q, nl, nr);
+        }
         for (int t = t0, i = 0; t < t1; t++, i++) {
             const int b = i & 1;
-            if (t + 1 < t1) {                            // the next tile's codes, in flight meanwhile
+            // the codes two tiles ahead, in flight meanwhile (one tile ahead
+            // left the producers waiting on the loads: 52 against 45 us for
+            // the 1280 x 720, D = 128 volume)
+            if (t + 2 < t1) {
                 tm.step(q);
-                fetch(q, nl, nr);
+                fetch(q, ml, mr);
             }
             if (i >= 2 && !bar_wait(ops_free + 8 * b, ((i - 2) >> 1) & 1, tries)) {
                 if (status) atomicExch(status, SIMSENSE_ERR_TIMEOUT);
@@ -386,8 +393,12 @@ cost_kernel(PairTable<N> pt, TileMap tm, int ntiles, int D, int nbits, KMask km,
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             bar_arrive(ops_full + 8 * b);
             cl = nl;
+            nl = ml;
 #pragma unroll
-            for (int j = 0; j < S::RPT; j++) cr[j] = nr[j];
+            for (int j = 0; j < S::RPT; j++) {
+                cr[j] = nr[j];
+                nr[j] = mr[j];
+            }
         }
     } else if (warp == kIssuerWarp) {
         // ---- the MMA issuer (one thread)

@@ -110,8 +110,9 @@ struct Tuning {
     int select_blocks = 1;   // selection kernel: 1 = one 1024-thread block per SM, 2 = two 512-thread blocks
 };
 
-// Programmatic dependent launch.  The main kernels of the stage are launched
-// with programmatic stream serialisation: the next kernel on the stream may
+// Programmatic dependent launch.  The census, cost and selection kernels are
+// launched with programmatic stream serialisation (the path kernel with a
+// plain launch, which measured faster after the cost kernel): the next kernel on the stream may
 // be scheduled once every block of the running one has started, and it waits
 // at its first instruction (pdl_wait: griddepcontrol.wait, which returns once
 // the previous kernel has completed and its memory is visible; at once when
@@ -126,6 +127,21 @@ __device__ __forceinline__ void pdl_wait()
 __device__ __forceinline__ void pdl_trigger()
 {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// The same launch without programmatic stream serialisation: the kernel
+// starts once its predecessor in the stream has completed (griddepcontrol.wait
+// then returns at once).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_plain(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.numAttrs = 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 template <typename... KArgs, typename... Args>

@@ -106,7 +106,11 @@ cudaError_t paths_chunk(const Params& p, const PairPtrs* pairs, int n, cudaStrea
     auto kernel = sgm_paths_kernel<NQ, G, NQH, GH, PF, N>;
     cudaError_t e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
     if (e != cudaSuccess) return e;
-    return launch_pdl(kernel, dim3(blocks), dim3(kPathThreads), smem, s, pt, n, p.W, p.H, p.P1, p.P2, p.paths);
+    // a plain launch: with programmatic stream serialisation after the cost
+    // kernel (whether that kernel lets its dependents start at its beginning
+    // or at its end) the 1280 x 720, D = 128 frame took 8% longer, cause not
+    // found; the path kernel still lets the selection start early
+    return launch_plain(kernel, dim3(blocks), dim3(kPathThreads), smem, s, pt, n, p.W, p.H, p.P1, p.P2, p.paths);
 }
 
 template <int NQ, int G, int NQH, int GH, int N>
