@@ -929,8 +929,8 @@ def main():
             h.close()
         return rep.max_over_ranks(el, dev)
 
-    by_k = {kf: world * e2e_steps / e2e_run(kf) for kf in (1, 2, 3, 4)}
-    best_k = max((2, 3, 4), key=lambda kf: by_k[kf])
+    by_k = {kf: world * e2e_steps / e2e_run(kf) for kf in (1, 2, 3, 4, 6, 8)}
+    best_k = max((2, 3, 4, 6, 8), key=lambda kf: by_k[kf])
     e2e = {"value": by_k[best_k], "unit": UNIT,
            "h2d_bytes_per_step": 2 * wl.W * wl.H, "d2h_bytes_per_step": 4 * wl.W * wl.H,
            "steps": e2e_steps, "frames_in_flight": best_k,
