@@ -151,7 +151,7 @@ KERNEL_SOURCES = {
 MEASURED_DRAM = {
     "1280x720_D128_census7x7_8path": {
         "census": (1855744, 1024, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
-        "cost": (14936576, 31500800, "52eb3a6f1b23f3163bbdc1692ebd48afd1e09980"),
+        "cost": (14936576, 31500800, "75f1f95ce775e3e03b6fdf09f3b42f7ba1b88054"),
         "paths": (536728064, 884464128, "798c2386b591a8b3b63ad3976906ae4877a22974"),
         "select": (943777792, 3174912, "9ff7efd5fe90fb3ca2008e966dd646ec5b564c1f"),
     },

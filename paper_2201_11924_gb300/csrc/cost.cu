@@ -23,8 +23,8 @@
 // A tile is 128 left pixels x0 .. x0 + 127 of one row.  A persistent block
 // (one per SM: it holds all 512 TMEM columns) takes a contiguous range of
 // tiles with three kinds of warps working on different tiles at once:
-//  - 4 producer warps load the codes of the next tile (prefetched one tile
-//    ahead) and expand the left codes (A, 128 x 32 KS bytes) and the right
+//  - 4 producer warps load the codes of the tile two ahead (prefetched two
+//    tiles ahead) and expand the left codes (A, 128 x 32 KS bytes) and the right
 //    codes of pixels x0 + 127 - n, n < Dp + 128 (B, descending, so that d
 //    grows with n) to e4m3 in one of two operand buffers, in the K-major
 //    core-matrix layout of the tensor-core descriptors (8 rows x 16 bytes per
