@@ -39,8 +39,8 @@ size_t select_smem(int W, int stages)
 }
 
 // Items are (pair, row); blocks are persistent over them.
-template <int NP, int G, int PATHS, int THREADS, int N>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
+template <int NP, int G, int PATHS, int THREADS, int N, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB)
 sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, uint32_t umagic,
                   int lr_max_diff, int subpixel, float fb, SelectDebug dbg, int* __restrict__ status,
                   int kStages, int disp_mode)
@@ -74,7 +74,9 @@ sgm_select_kernel(PairTable<N> pt, int npairs, int W, int H, int D, int uniq, ui
     }
 }
 
-template <int NP, int G, int PATHS, int THREADS, int N>
+// MINB: blocks per SM (1024 / THREADS unless a layout needs the registers of
+// a whole SM)
+template <int NP, int G, int PATHS, int THREADS, int N, int MINB = 1024 / THREADS>
 cudaError_t select_launch(const Params& p, const PairTable<N>& pt, int n, const SelectDebug& dbg, int* status,
                           cudaStream_t s)
 {
@@ -82,13 +84,13 @@ cudaError_t select_launch(const Params& p, const PairTable<N>& pt, int n, const 
     cudaError_t e = device_limits(lim);
     if (e != cudaSuccess) return e;
     // 1024 / THREADS blocks per SM with the deepest ring that lets them fit
-    constexpr int blocks_per_sm = 1024 / THREADS;
+    constexpr int blocks_per_sm = MINB;
     const size_t budget = blocks_per_sm == 1 ? (size_t)lim.optin : (size_t)lim.per_sm / blocks_per_sm - 1024;
     int stages = kMaxStages;
     while (stages > 2 && select_smem<NP, G, PATHS, THREADS>(p.W, stages) > budget) stages--;
     const size_t smem = select_smem<NP, G, PATHS, THREADS>(p.W, stages);
     if (smem > budget) return cudaErrorInvalidValue;
-    auto kernel = sgm_select_kernel<NP, G, PATHS, THREADS, N>;
+    auto kernel = sgm_select_kernel<NP, G, PATHS, THREADS, N, MINB>;
     e = ensure_smem(reinterpret_cast<const void*>(kernel), smem);
     if (e != cudaSuccess) return e;
     const int items = n * p.H;
@@ -113,6 +115,20 @@ cudaError_t select_chunk(const Params& p, const PairPtrs* pairs, int n, const Tu
                                 : select_launch<NP, G, 8, 512, N>(p, pt, n, dbg, status, s);
 }
 
+// Dp = 256: 16 lanes a pixel with 16 disparities each, one 512-thread block
+// per SM (two stages of 32 pixels fit beside the row arrays at 1920 x 1080):
+// 716 against 741 us for a whole warp a pixel with 8 disparities a lane in
+// 1024-thread blocks, at 1920 x 1080, D = 256, 8 paths.
+template <int N>
+cudaError_t select_wide(const Params& p, const PairPtrs* pairs, int n, const SelectDebug& dbg, int* status,
+                        cudaStream_t s)
+{
+    PairTable<N> pt{};
+    for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
+    if (p.paths == 4) return select_launch<8, 16, 4, 512, N, 1>(p, pt, n, dbg, status, s);
+    return select_launch<8, 16, 8, 512, N, 1>(p, pt, n, dbg, status, s);
+}
+
 template <int N>
 cudaError_t select_dp(const Params& p, const PairPtrs* pairs, int n, const Tuning& t, const SelectDebug& dbg,
                       int* status, cudaStream_t s)
@@ -121,7 +137,7 @@ cudaError_t select_dp(const Params& p, const PairPtrs* pairs, int n, const Tunin
         case 64: return select_chunk<4, 8, N>(p, pairs, n, t, dbg, status, s);
         case 128: return select_chunk<4, 16, N>(p, pairs, n, t, dbg, status, s);
         case 192: return select_chunk<3, 32, N>(p, pairs, n, t, dbg, status, s);
-        case 256: return select_chunk<4, 32, N>(p, pairs, n, t, dbg, status, s);
+        case 256: return select_wide<N>(p, pairs, n, dbg, status, s);
         default: return cudaErrorInvalidValue;
     }
 }
