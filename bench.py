@@ -153,7 +153,7 @@ MEASURED_DRAM = {
         "census": (1855744, 1024, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
         "cost": (14936576, 31500800, "75f1f95ce775e3e03b6fdf09f3b42f7ba1b88054"),
         "paths": (536728064, 884464128, "798c2386b591a8b3b63ad3976906ae4877a22974"),
-        "select": (943777792, 3174912, "1e7b2ed0f128238889f8b9c9dc3bee9eb0b735b7"),
+        "select": (943777792, 3174912, "27fb1dc6158ce0a8a29e303e428d6eee2d481da3"),
     },
 }
 

@@ -115,18 +115,20 @@ cudaError_t select_chunk(const Params& p, const PairPtrs* pairs, int n, const Tu
                                 : select_launch<NP, G, 8, 512, N>(p, pt, n, dbg, status, s);
 }
 
-// Dp = 256: 16 lanes a pixel with 16 disparities each, one 512-thread block
-// per SM (two stages of 32 pixels fit beside the row arrays at 1920 x 1080):
-// 716 against 741 us for a whole warp a pixel with 8 disparities a lane in
-// 1024-thread blocks, at 1920 x 1080, D = 256, 8 paths.
-template <int N>
+// Dp = 64 and 256: G lanes a pixel with 16 disparities each, one 512-thread
+// block per SM.  At 1920 x 1080, D = 256, 8 paths: 716 against 741 us for a
+// whole warp a pixel with 8 disparities a lane in 1024-thread blocks; at
+// 320 x 240, D = 64, 4 paths: 14.0 against 14.6 us for 8 lanes with 8
+// disparities each.  (At Dp = 128 the same shape, 8 lanes with 16 each, took
+// 180 against 175 us.)
+template <int G, int N>
 cudaError_t select_wide(const Params& p, const PairPtrs* pairs, int n, const SelectDebug& dbg, int* status,
                         cudaStream_t s)
 {
     PairTable<N> pt{};
     for (int i = 0; i < n; i++) pt.p[i] = pairs[i];
-    if (p.paths == 4) return select_launch<8, 16, 4, 512, N, 1>(p, pt, n, dbg, status, s);
-    return select_launch<8, 16, 8, 512, N, 1>(p, pt, n, dbg, status, s);
+    if (p.paths == 4) return select_launch<8, G, 4, 512, N, 1>(p, pt, n, dbg, status, s);
+    return select_launch<8, G, 8, 512, N, 1>(p, pt, n, dbg, status, s);
 }
 
 template <int N>
@@ -134,10 +136,10 @@ cudaError_t select_dp(const Params& p, const PairPtrs* pairs, int n, const Tunin
                       int* status, cudaStream_t s)
 {
     switch (p.Dp) {
-        case 64: return select_chunk<4, 8, N>(p, pairs, n, t, dbg, status, s);
+        case 64: return select_wide<4, N>(p, pairs, n, dbg, status, s);
         case 128: return select_chunk<4, 16, N>(p, pairs, n, t, dbg, status, s);
         case 192: return select_chunk<3, 32, N>(p, pairs, n, t, dbg, status, s);
-        case 256: return select_wide<N>(p, pairs, n, dbg, status, s);
+        case 256: return select_wide<16, N>(p, pairs, n, dbg, status, s);
         default: return cudaErrorInvalidValue;
     }
 }
