@@ -150,10 +150,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_DRAM = {
     "1280x720_D128_census7x7_8path": {
-        "census": (1855744, 1024, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
-        "cost": (14936576, 31500800, "75f1f95ce775e3e03b6fdf09f3b42f7ba1b88054"),
-        "paths": (536728064, 884464128, "798c2386b591a8b3b63ad3976906ae4877a22974"),
-        "select": (943777792, 3174912, "27fb1dc6158ce0a8a29e303e428d6eee2d481da3"),
+        "census": (1855232, 0, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
+        "cost": (14937088, 31800576, "75f1f95ce775e3e03b6fdf09f3b42f7ba1b88054"),
+        "paths": (538493952, 883846400, "798c2386b591a8b3b63ad3976906ae4877a22974"),
+        "select": (943790848, 3224320, "27fb1dc6158ce0a8a29e303e428d6eee2d481da3"),
     },
 }
 
