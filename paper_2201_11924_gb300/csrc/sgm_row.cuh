@@ -71,17 +71,6 @@ __device__ __forceinline__ void lds_words(uint32_t (&w)[(NP + 1) / 2], const uin
 // hit different shared-memory banks.
 __device__ __forceinline__ int kr(int xr) { return xr + (xr >> 5); }
 
-// Sum of two pairs of 16-bit integers below 2048 with add.f16x2 (the FMA
-// pipe): as an f16, the bit pattern n < 2048 is n * 2^-24 (subnormal below
-// 1024, exponent field 1 above), so the exact sum is representable and its
-// bit pattern is the integer sum.
-__device__ __forceinline__ uint32_t hadd2_bits(uint32_t a, uint32_t b)
-{
-    uint32_t d;
-    asm("add.rn.f16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
-    return d;
-}
-
 // Minimum of a 32-bit value over the G lanes of a group (shuffle butterfly).
 template <int G>
 __device__ __forceinline__ uint32_t group_min32(uint32_t v)
@@ -112,10 +101,13 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
     const int d0 = chunk * DPT;
     const size_t pix = (size_t)y * W + x;
     // path sums: ev[k] holds cells (4k, 4k+2), od[k] cells (4k+1, 4k+3) as
-    // 16-bit halves, accumulated with add.f16x2 (hadd2_bits): a sum of at most
-    // 8 bytes is at most 2040, below 2048, so every partial sum is exact and
-    // the adds run on the FMA pipe, beside the byte extraction and the minima
-    // on the ALU pipe
+    // 16-bit halves.  od sums the odd bytes (b1, b3) of every path word, one
+    // permute each; a sum of at most 8 bytes (2040) never carries into the
+    // upper half.  ev sums the whole words modulo 2^32 (carries between bytes
+    // included) and then takes 256 * od off: sum(b0 + 2^8 b1 + 2^16 b2 +
+    // 2^24 b3) - 2^8 sum(b1 + 2^16 b3) = sum(b0) + 2^16 sum(b2) < 2^32, so the
+    // modular result is exact.  No byte mask: the adds and the one multiply-add
+    // issue beside the permutes and minima instead of on their pipe.
     uint32_t ev[NW], od[NW];
 #pragma unroll
     for (int r = 0; r < PATHS; r++) {
@@ -123,11 +115,13 @@ __device__ __forceinline__ void select_pixel(const uint8_t* src, int x, bool act
         lds_words<NP>(a, src + r * Dp + d0);
 #pragma unroll
         for (int k = 0; k < NW; k++) {
-            const uint32_t e = a[k] & 0x00ff00ffu, o = __byte_perm(a[k], 0, 0x4341);
-            ev[k] = r == 0 ? e : hadd2_bits(ev[k], e);
-            od[k] = r == 0 ? o : hadd2_bits(od[k], o);
+            const uint32_t o = __byte_perm(a[k], 0, 0x4341);
+            ev[k] = r == 0 ? a[k] : ev[k] + a[k];
+            od[k] = r == 0 ? o : od[k] + o;
         }
     }
+#pragma unroll
+    for (int k = 0; k < NW; k++) ev[k] -= od[k] * 256u;
     // padded cells d >= D (their path bytes carry no meaning) read as
     // S = 0xffff: their keys lose to every real cell's (S <= 2040), in the
     // winner, in the right-view minimum (d = 0 is real for every right

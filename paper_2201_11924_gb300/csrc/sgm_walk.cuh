@@ -216,10 +216,11 @@ __device__ __forceinline__ void walk_steps(int base, int n, int len, uint32_t ri
             const uint32_t tE = vmin2(vmin3(Lc[2 * q], Lp[2 * q + 1], shift_pair(Oprev, Lp[2 * q + 1])), cap);
             // O = (d1, d3): d - 1 is E = (d0, d2), d + 1 is (d2, d4)
             const uint32_t tO = vmin2(vmin3(Lc[2 * q + 1], Lp[2 * q], shift_pair(Lp[2 * q], Enext)), cap);
-            // cost bytes (c0, c1, c2, c3) -> (c0, c2) and (c1, c3)
-            const uint32_t cE = cw[q] & 0x00ff00ffu;
+            // cost bytes (c0, c1, c2, c3) -> (c1, c3) by a permute, and
+            // (c0, c2) = word - 256 (c1, c3), folded into the sum as a
+            // multiply-add (off the permute and minimum pipe, unlike a mask)
             const uint32_t cO = __byte_perm(cw[q], 0, 0x4341);
-            L[2 * q] = tE + cE - mm;           // no borrow: every half of t is >= m'
+            L[2 * q] = tE + cw[q] - mm - cO * 256u;   // no borrow: every half of t is >= m'
             L[2 * q + 1] = tO + cO - mm;
             out[q] = L[2 * q + 1] * 256u + L[2 * q];            // bytes (L0, L1, L2, L3)
         }
