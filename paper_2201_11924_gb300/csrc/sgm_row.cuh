@@ -71,10 +71,24 @@ __device__ __forceinline__ void lds_words(uint32_t (&w)[(NP + 1) / 2], const uin
 // hit different shared-memory banks.
 __device__ __forceinline__ int kr(int xr) { return xr + (xr >> 5); }
 
-// Minimum of a 32-bit value over the G lanes of a group (shuffle butterfly).
+// Minimum of a 32-bit value over the G lanes of a group: for 8 to 32 lanes
+// one whole-warp redux.sync per group, the other groups' lanes offering
+// 0xffffffff (fewer instructions than a shuffle butterfly), for smaller
+// groups the butterfly.  Called by the whole warp.
 template <int G>
 __device__ __forceinline__ uint32_t group_min32(uint32_t v)
 {
+    if constexpr (G >= 8) {
+        constexpr int NG = 32 / G;
+        const int grp = (threadIdx.x & 31) / G;
+        uint32_t res = 0;
+#pragma unroll
+        for (int g = 0; g < NG; g++) {
+            const uint32_t r = __reduce_min_sync(0xffffffffu, grp == g ? v : 0xffffffffu);
+            res = grp == g ? r : res;
+        }
+        return res;
+    }
 #pragma unroll
     for (int o = 1; o < G; o <<= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;

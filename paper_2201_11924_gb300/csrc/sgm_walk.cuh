@@ -161,8 +161,12 @@ __device__ __forceinline__ void store_words(uint8_t* p, const uint32_t (&w)[NQ])
 }
 
 // (m, m) with m the minimum over the group's cells: a three-input-min tree
-// over the lane's 2*NQ pairs, the two halves, then the group (one redux.sync
-// for a whole warp, a shuffle butterfly for a partial-warp group).
+// over the lane's 2*NQ pairs, the two halves, then the group.  For groups of
+// 8 to 32 lanes, one whole-warp redux.sync per group, in which the other
+// groups' lanes offer 0xffffffff: 32 / G independent reductions, a shorter
+// chain than a butterfly of log2(G) dependent shuffles (the minimum m' is on
+// the step-to-step chain of the recurrence); smaller groups use the
+// butterfly.
 template <int NQ, int G>
 __device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[2 * NQ])
 {
@@ -177,8 +181,16 @@ __device__ __forceinline__ uint32_t group_min(const uint32_t (&L)[2 * NQ])
         mn = vmin3(vmin3(L[0], L[1], L[2]), vmin3(L[3], L[4], L[5]), vmin2(L[6], L[7]));
     }
     mn = vmin2(mn, __byte_perm(mn, 0, 0x1032));
-    if constexpr (G == 32) {
-        return __reduce_min_sync(0xffffffffu, mn);
+    if constexpr (G >= 8) {
+        constexpr int NG = 32 / G;
+        const int grp = (threadIdx.x & 31) / G;
+        uint32_t res = 0;
+#pragma unroll
+        for (int g = 0; g < NG; g++) {
+            const uint32_t r = __reduce_min_sync(0xffffffffu, grp == g ? mn : 0xffffffffu);
+            res = grp == g ? r : res;
+        }
+        return res;
     } else {
 #pragma unroll
         for (int o = 1; o < G; o <<= 1) mn = vmin2(mn, __shfl_xor_sync(0xffffffffu, mn, o));
