@@ -150,10 +150,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_DRAM = {
     "1280x720_D128_census7x7_8path": {
-        "census": (1855232, 0, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
-        "cost": (14937088, 31800576, "75f1f95ce775e3e03b6fdf09f3b42f7ba1b88054"),
-        "paths": (538493952, 883846400, "798c2386b591a8b3b63ad3976906ae4877a22974"),
-        "select": (943790848, 3224320, "27fb1dc6158ce0a8a29e303e428d6eee2d481da3"),
+        "census": (1855488, 0, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
+        "cost": (14917888, 31666432, "75f1f95ce775e3e03b6fdf09f3b42f7ba1b88054"),
+        "paths": (560134656, 885368832, "7608e5e1ed7f8a9871ce0a9dd0d139216a1b1cad"),
+        "select": (943855872, 3319808, "dc5c9b4f604d30ed20e99f687041de8c4af6024c"),
     },
 }
 
