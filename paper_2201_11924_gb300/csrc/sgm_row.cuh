@@ -88,10 +88,11 @@ __device__ __forceinline__ uint32_t group_min32(uint32_t v)
             res = grp == g ? r : res;
         }
         return res;
-    }
+    } else {
 #pragma unroll
-    for (int o = 1; o < G; o <<= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+        for (int o = 1; o < G; o <<= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+        return v;
+    }
 }
 
 // One pixel of the row for one lane group: sum, winner, uniqueness, offers to
