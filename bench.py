@@ -150,10 +150,10 @@ KERNEL_SOURCES = {
 }
 MEASURED_DRAM = {
     "1280x720_D128_census7x7_8path": {
-        "census": (1855488, 0, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
-        "cost": (14917888, 31666432, "75f1f95ce775e3e03b6fdf09f3b42f7ba1b88054"),
-        "paths": (560134656, 885368832, "7608e5e1ed7f8a9871ce0a9dd0d139216a1b1cad"),
-        "select": (943855872, 3319808, "dc5c9b4f604d30ed20e99f687041de8c4af6024c"),
+        "census": (1855232, 0, "56aba98b2aec52d52bdbada4a33bc0c40c7d6642"),
+        "cost": (14918656, 31478016, "75f1f95ce775e3e03b6fdf09f3b42f7ba1b88054"),
+        "paths": (565320960, 885341440, "7608e5e1ed7f8a9871ce0a9dd0d139216a1b1cad"),
+        "select": (943805184, 2999552, "36b7eada1e28f2e124cfcf2d77d9af6a325dff36"),
     },
 }
 
